@@ -1,0 +1,214 @@
+/*
+ * figaro.h -- C ABI of the GB300 FiGaRo library.
+ *
+ * FiGaRo (Olteanu, Vortmeier, Zivanovic, "Givens Rotations for QR Decomposition, SVD
+ * and PCA over Database Joins", arXiv 2204.00525) computes the upper-triangular R of
+ * the QR decomposition of A[:, Y], the data columns of the natural join of an acyclic
+ * database, without materialising the join (§2 "Input"/"Output", Theorem of §6), and
+ * from R the SVD and PCA of A (§8.2-8.3).  Every step runs in CUDA kernels on one
+ * GPU; the host code only validates, plans and launches.
+ *
+ * Conventions shared by every entry point
+ *   - Status: every function returns an int, FIGARO_OK (0) on success, else one of
+ *     figaro_status.  figaro_error_string() names a status; figaro_last_error()
+ *     returns a message with details about the most recent failure of this thread.
+ *   - Memory: in FIGARO_MEM_DEVICE mode (the default) every data pointer (key columns,
+ *     data, R, sigma, V, components, eigvals) is a device pointer of the current CUDA
+ *     device; in FIGARO_MEM_HOST mode they are host pointers (pinned memory gives
+ *     asynchronous copies) and the library copies inputs in and results out on the
+ *     plan's stream.  The caller owns all input and output buffers; inputs must stay
+ *     valid and unchanged while a call that reads them is running.  The plan owns its
+ *     device workspace and frees it in figaro_plan_destroy.
+ *   - Streams: all device work is enqueued on the stream given to figaro_plan (a
+ *     cudaStream_t passed as void*, NULL for the legacy default stream).  The compute
+ *     calls block the calling host thread only at their end, to read one device error
+ *     word; they may be called again on the same plan once they have returned.
+ *   - Column order of A[:, Y], R, V and the components: relation order 0..n_rel-1,
+ *     then data-column order inside each relation (the [T_1 ... T_r] layout of Alg. 4).
+ *   - Threads: a plan must not be used by two host threads at once.
+ */
+#ifndef FIGARO_H
+#define FIGARO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum figaro_status {
+  FIGARO_OK = 0,
+  FIGARO_ERR_INVALID_ARG = 1,   /* a null pointer, negative size, bad enum, ld too small  */
+  FIGARO_ERR_INVALID_TREE = 2,  /* parent[] is not a tree, or it is not a join tree (§2:
+                                   the relations holding an attribute must be connected),
+                                   or a key attribute occurs in a single relation         */
+  FIGARO_ERR_NOT_REDUCED = 3,   /* require_reduced was set and a tuple does not join     */
+  FIGARO_ERR_OVERFLOW = 4,      /* a join count (§5) does not fit in 64 bits              */
+  FIGARO_ERR_NOMEM = 5,         /* device or host allocation failed                      */
+  FIGARO_ERR_TIMEOUT = 6,       /* reserved for bounded device waits                     */
+  FIGARO_ERR_CUDA = 7,          /* a CUDA runtime call failed (see figaro_last_error)     */
+  FIGARO_ERR_KEY_RANGE = 8,     /* a key value lies outside the range seen by figaro_plan */
+  FIGARO_ERR_NOT_SORTED = 9,    /* presorted was set but a relation is not sorted         */
+  FIGARO_ERR_UNSUPPORTED = 10   /* a size limit of this build (see below) is exceeded     */
+};
+
+enum { FIGARO_KEY_I64 = 0, FIGARO_KEY_I32 = 1 };
+enum { FIGARO_COL_MAJOR = 0, FIGARO_ROW_MAJOR = 1 };
+enum { FIGARO_PREC_FP64 = 0, FIGARO_PREC_MIXED = 1 };
+enum { FIGARO_MEM_DEVICE = 0, FIGARO_MEM_HOST = 1 };
+
+/* One relation S_i (§2 "Relations and Joins").
+ *   n_rows    M_i >= 1, at most 2^31 - 1.
+ *   n_keys    number of key (join) attributes K_i (0 allowed: a relation joined by
+ *             Cartesian product).  At most 8.
+ *   key_attr  host array [n_keys]: global attribute id (>= 0) of each key column.  The
+ *             natural join equates equal ids.  Every id must occur in at least two
+ *             relations (a key attribute is a join attribute).
+ *   key_cols  host array [n_keys] of pointers, each to n_rows keys of key_type.
+ *   n_data    N_i >= 0 data columns; sum over relations must be in [1, 1024].
+ *   data      n_rows x n_data float64 matrix, element (r, c) at
+ *             data[c*ld + r] (FIGARO_COL_MAJOR, ld >= n_rows) or data[r*ld + c]
+ *             (FIGARO_ROW_MAJOR, ld >= n_data).                                       */
+typedef struct figaro_relation {
+  int64_t n_rows;
+  int32_t n_keys;
+  int32_t key_type;
+  const int32_t* key_attr;
+  const void* const* key_cols;
+  int32_t n_data;
+  int32_t layout;
+  int64_t ld;
+  const double* data;
+} figaro_relation;
+
+/* The database and its join tree tau (§2 "Input"): parent[i] is the parent of
+ * relation i, -1 for the single root.  Host memory, read only during figaro_plan. */
+typedef struct figaro_join_tree {
+  int32_t n_rel;
+  const figaro_relation* rels;
+  const int32_t* parent;
+} figaro_join_tree;
+
+/* Options.  Initialise with figaro_default_options.
+ *   precision        FIGARO_PREC_FP64: every step in float64.  FIGARO_PREC_MIXED:
+ *                    counts exact, head/tail scans in float64, the TSQR leaf tiles in
+ *                    float32 on equilibrated columns, the TSQR tree and R in float64.
+ *   presorted        1: every relation is already sorted by its key (the order §5
+ *                    assumes: attributes shared with the parent first, then the rest,
+ *                    each part in ascending attribute id, values ascending); the sort
+ *                    is skipped and the order is verified (FIGARO_ERR_NOT_SORTED).
+ *   require_reduced  1: fail with FIGARO_ERR_NOT_REDUCED when a tuple does not join
+ *                    (the paper assumes fully reduced input, §2); 0 (default): such
+ *                    tuples are given weight 0, which is exact since they are not in A.
+ *   mem              FIGARO_MEM_DEVICE or FIGARO_MEM_HOST (see the conventions).
+ *   stage_timing     1: time every stage with CUDA events (figaro_stage_times).      */
+typedef struct figaro_options {
+  int32_t precision;
+  int32_t presorted;
+  int32_t require_reduced;
+  int32_t mem;
+  int32_t stage_timing;
+  int32_t reserved[11];
+} figaro_options;
+
+typedef struct figaro_plan_s* figaro_plan_t;
+
+/* Sizes of a plan and of its most recent figaro_qr_r call. */
+typedef struct figaro_plan_info {
+  int32_t n_rel;
+  int32_t n_cols;              /* N, the order of R                                   */
+  int64_t input_cells;         /* sum_i M_i (N_i + K_i)                               */
+  int64_t input_bytes;         /* bytes of keys and data read per call                */
+  int64_t workspace_bytes;     /* device workspace held by the plan                   */
+  int64_t r0_rows;             /* rows of R0 after the last call (<= sum_i M_i)       */
+  int64_t launches;            /* kernels launched by the last compute call           */
+  double tsqr_leaf_flops;      /* algorithmic flops of the TSQR leaf tiles, last call */
+} figaro_plan_info;
+
+/* Fill *opt with the defaults (FP64, not presorted, reduce, device memory, no timing). */
+void figaro_default_options(figaro_options* opt);
+
+/* Validate the database and join tree, scan the key ranges and allocate the device
+ * workspace (sized from the bound of the Theorem of §6: R0 has at most sum M_i rows).
+ * Key ranges are fixed here: later calls fail with FIGARO_ERR_KEY_RANGE if a key
+ * leaves them.  The relation pointers are recorded and read again by every compute
+ * call.  Blocks the host until the key-range scan is done.
+ * Errors: INVALID_ARG, INVALID_TREE, UNSUPPORTED (more than 64 bits of packed key in
+ * one relation, sizes above the limits), NOMEM, CUDA.  *out is NULL on failure.    */
+int figaro_plan(const figaro_join_tree* tree, const figaro_options* opt, void* stream,
+                figaro_plan_t* out);
+
+/* R (§2 "Output"): sort and segment every relation by key, compute the count
+ * aggregates (Alg. 3), the heads and tails (Alg. 4 with Alg. 2) and triangularize R0
+ * with a tall-skinny QR (§7).  Writes the N x N upper-triangular R, row-major with
+ * leading dimension ldr >= N, normalised to a non-negative diagonal (§2: unique for
+ * full rank); entries below the diagonal are written as 0.
+ * Errors: INVALID_ARG, NOT_REDUCED, OVERFLOW, KEY_RANGE, NOT_SORTED, CUDA.        */
+int figaro_qr_r(figaro_plan_t plan, double* R, int64_t ldr);
+
+/* Singular values and right singular vectors of A (§8.2: those of R).  Computes R as
+ * figaro_qr_r does, then a one-sided Jacobi SVD of R in float64.  sigma[N] is
+ * descending; V is N x N row-major, column j the j-th right singular vector, each
+ * column signed so that its largest-magnitude entry is positive.  R may be NULL; if
+ * not, R is also written (row-major, leading dimension N). */
+int figaro_svd(figaro_plan_t plan, double* sigma, double* V, double* R);
+
+/* Top-k principal components of A (§8.3, data not centred, as in the paper's
+ * experiments): components is N x k row-major (column j = j-th component, the
+ * right singular vector of the j-th largest singular value), eigvals[k] = sigma^2.
+ * 1 <= k <= N. */
+int figaro_pca(figaro_plan_t plan, int32_t k, double* components, double* eigvals);
+
+/* Release the plan's workspace (waits for its stream).  NULL is accepted. */
+int figaro_plan_destroy(figaro_plan_t plan);
+
+/* Sizes of the plan and of its last call. */
+int figaro_plan_get_info(figaro_plan_t plan, figaro_plan_info* info);
+
+/* Stage times in milliseconds summed over the compute calls since the last reset,
+ * when the plan was made with stage_timing = 1 (else zeros).  Stages:
+ *   0 key packing and radix sort, 1 segmentation, 2 count aggregates (Alg. 3),
+ *   3 heads and tails of the relations (Alg. 4 heads_and_tails),
+ *   4 join of children and projection (Alg. 4 process_and_join_children,
+ *     project_away_join_attributes, root), 5 TSQR leaf tiles, 6 TSQR tree and final
+ *   QR, 7 SVD.  counts[s] is the number of kernel launches of stage s in the same
+ *   period.  Returns the number of stages (8) or a negative status.                */
+int figaro_stage_times(figaro_plan_t plan, double* ms, int64_t* counts, int32_t n);
+int figaro_reset_stage_times(figaro_plan_t plan);
+
+/* Copy an intermediate array of relation `rel` from the last compute call to host
+ * memory, for tests and diagnostics (a synchronous copy of at most `bytes` bytes).
+ * Returns the number of bytes the array holds (>= 0) or a negative status.
+ *   FIGARO_DBG_SIZES     int64[8]: M, G (groups of X_i), P (groups of X_p), tail
+ *                        rows, generalized-tail rows, root rows, K, N_sub
+ *   FIGARO_DBG_PERM      int32[M]: row of the input at each sorted position
+ *   FIGARO_DBG_GROUP_OFF int32[G+1]: first sorted position of every group
+ *   FIGARO_DBG_COUNTS    uint64[4*G]: rows_per_key, Theta_down, full_join_size,
+ *                        Phi_circ of every group (group-major)
+ *   FIGARO_DBG_PCOUNTS   uint64[2*P]: Phi_down, Phi_up of every X_p group
+ *   FIGARO_DBG_TAILS     float64[(M-G) x N_i] column-major: sqrt(Phi_circ) T(S^{x})
+ *                        of every group, groups in key order
+ *   FIGARO_DBG_HEADS     float64[G x N_i] column-major: H(S^{x}) of every group
+ *   FIGARO_DBG_GEN_TAILS float64[(G-P) x N_sub] column-major: generalized tails of
+ *                        the projection (internal non-root relations)
+ *   FIGARO_DBG_DATA      float64[P x N_sub] column-major: the generalized heads
+ *                        passed to the parent (internal non-root relations)
+ *   FIGARO_DBG_ROOT_ROWS float64[G x N] column-major: the root's Data rows        */
+enum {
+  FIGARO_DBG_SIZES = 0, FIGARO_DBG_PERM = 1, FIGARO_DBG_GROUP_OFF = 2, FIGARO_DBG_COUNTS = 3,
+  FIGARO_DBG_PCOUNTS = 4, FIGARO_DBG_TAILS = 5, FIGARO_DBG_HEADS = 6, FIGARO_DBG_GEN_TAILS = 7,
+  FIGARO_DBG_DATA = 8, FIGARO_DBG_ROOT_ROWS = 9
+};
+int64_t figaro_debug_read(figaro_plan_t plan, int32_t rel, int32_t what, void* dst, int64_t bytes);
+
+/* Name of a status code (static storage). */
+const char* figaro_error_string(int status);
+
+/* Details of the most recent failure on the calling thread ("" if none). */
+const char* figaro_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FIGARO_H */

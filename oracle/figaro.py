@@ -46,8 +46,9 @@ class Block:
         return f"Block({self.kind}, S{self.rel + 1}, {self.rows.shape})"
 
 
-def figaro_r0(db, counts=None):
-    """Alg. 4 on a fully reduced database: returns the list of R0 blocks."""
+def figaro_r0(db, counts=None, record=None):
+    """Alg. 4 on a fully reduced database: returns the list of R0 blocks.  If ``record``
+    is a dict, record[i] receives the (Data, scales) that S_i returns to its parent."""
     counts = compute_counts(db) if counts is None else counts
     blocks = []
 
@@ -101,6 +102,8 @@ def figaro_r0(db, counts=None):
             # a leaf: X_i = X_p (every join attribute of a leaf is shared with its
             # parent), so Data already has one row per x_p and Alg. 4 returns it as is.
             index = {keys[g]: g for g in range(G)}
+            if record is not None:
+                record[i] = (Data.copy(), scales.copy())
             return {"Data": Data, "scales": scales, "index": index, "cols": sub_cols}
         if db.parent[i] >= 0:
             # project_away_join_attributes: groups are sorted with X_p first, so the
@@ -122,6 +125,8 @@ def figaro_r0(db, counts=None):
                 scales2[p] = np.sqrt(counts[i]["down"][xp])
                 index[xp] = p
             blocks.append(Block("gen_tails", i, sub_cols, np.concatenate(gts)))
+            if record is not None:
+                record[i] = (Data2.copy(), scales2.copy())
             return {"Data": Data2, "scales": scales2, "index": index, "cols": sub_cols}
         blocks.append(Block("root", i, sub_cols, Data))
         return None

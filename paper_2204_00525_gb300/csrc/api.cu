@@ -1,0 +1,1016 @@
+// C ABI (include/figaro.h): validation, planning, workspace and the per-call pipeline.
+//
+// figaro_plan checks the database and join tree (§2), fixes the key packing and sizes
+// one device arena from the bounds of the Theorem of §6 (R0 has at most sum M_i rows;
+// groups never outnumber rows).  Every compute call then enqueues, on one stream and
+// without host synchronisation until a final error-word read:
+//   pack + radix sort + segmentation of every relation        (§5 sort assumption)
+//   Alg. 3 pass 1 (post-order) and pass 2 (pre-order)         (§5)
+//   heads_and_tails of every relation                         (Alg. 4, Alg. 2)
+//   process_and_join_children + project_away, root Data       (Alg. 4, post-order)
+//   TSQR of the R0 blocks and the final QR                    (§7)
+//   Jacobi SVD of R for figaro_svd / figaro_pca               (§8.2-8.3)
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace fig {
+
+static thread_local std::string g_last_error;
+
+static int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define FIG_CUDA(call)                                                                     \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(FIGARO_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+  } while (0)
+
+constexpr int kStages = 8;
+constexpr int64_t kBetaMax = 1 << 20;
+
+struct Node {
+  int id = 0, parent = -1;
+  std::vector<int> children;
+  bool leaf = true, root = false;
+  int64_t M = 0;
+  int K = 0, N = 0, key_type = 0, layout = 0;
+  int64_t ld = 0;
+  std::vector<int> key_attr;
+  std::vector<const void*> key_ptr;     // as given by the caller
+  const double* data = nullptr;         // as given by the caller
+  std::vector<void*> dkey;              // device copies (host-memory mode)
+  double* ddata = nullptr;              // device copy (host-memory mode)
+  // packing: X_p attributes (ascending id) in the high bits, then the rest
+  std::vector<int> pack_attr, pack_col, shift;
+  int bits = 0, rest_bits = 0;
+  // columns
+  int col_off = 0, N_sub = 0;
+  std::vector<int> sub_cols;
+  std::vector<int2> coldesc;
+  NodeBuf b{};
+  int64_t n_tiles = 0;
+  ChildLink link[kMaxChildren]{};      // one per child (filled for the parent's passes)
+};
+
+}  // namespace fig
+
+struct figaro_plan_s {
+  std::vector<fig::Node> nodes;
+  int root = 0, N = 0;
+  figaro_options opt{};
+  cudaStream_t st = nullptr;
+  int device = 0;
+  std::vector<int> post, pre;
+  std::vector<long long> amin;
+  std::vector<int> abits;
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  int* err_dev = nullptr;
+  int* err_host = nullptr;             // pinned: [0] error word, [4 + 4 i ..] sizes of node i
+  double* beta = nullptr;
+  int64_t beta_len = 0;
+  int32_t* radix_hist = nullptr;
+  int32_t* radix_scan_tmp = nullptr;
+  std::vector<fig::TsqrBlock> blocks;
+  fig::TsqrBlock* blocks_dev = nullptr;
+  void* tsqr_scratch = nullptr;
+  int stack_rows = 0;
+  double* stack = nullptr;
+  double* Rtmp = nullptr;
+  double* svdW = nullptr;
+  double* svdV = nullptr;
+  double* sig = nullptr;
+  double* Vtmp = nullptr;
+  double* hostbuf_dev = nullptr;        // staging for host-memory outputs
+  int64_t launches = 0;
+  cudaEvent_t ev[fig::kStages + 1]{};
+  double stage_ms[fig::kStages]{};
+  int64_t stage_launch[fig::kStages]{};
+  int64_t input_cells = 0, input_bytes = 0;
+  double leaf_flops = 0.0;
+  int64_t r0_rows = 0;
+};
+
+namespace fig {
+
+// ------------------------------------------------------------------ arena
+struct Arena {
+  char* base = nullptr;
+  size_t off = 0;
+  template <typename T>
+  T* take(int64_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += (size_t)(count > 0 ? count : 1) * sizeof(T);
+    return p;
+  }
+};
+
+static int bits_for(unsigned long long range) {
+  int b = 0;
+  while (b < 64 && (range >> b) != 0ull) ++b;
+  return b;
+}
+
+// Lays out every device buffer of the plan; with a.base == nullptr only measures.
+static void layout(figaro_plan_s& P, Arena& a) {
+  const bool mixed = P.opt.precision == FIGARO_PREC_MIXED;
+  int64_t maxM = 1;
+  for (auto& n : P.nodes) maxM = std::max(maxM, n.M);
+  P.err_dev = a.take<int>(4);
+  P.beta_len = std::min<int64_t>(maxM + 1, kBetaMax);
+  P.beta = a.take<double>(P.beta_len);
+  const int64_t rt = radix_tiles(maxM);
+  P.radix_hist = a.take<int32_t>(2 * 256 * rt);
+  P.radix_scan_tmp = a.take<int32_t>(scan_tmp_elems(256 * rt));
+  for (auto& n : P.nodes) {
+    NodeBuf& b = n.b;
+    const int64_t M = n.M;
+    const int nch = (int)n.children.size();
+    if (P.opt.mem == FIGARO_MEM_HOST) {
+      for (int k = 0; k < n.K; ++k)
+        n.dkey[k] = n.key_type == FIGARO_KEY_I32 ? (void*)a.take<int32_t>(M) : (void*)a.take<int64_t>(M);
+      n.ddata = a.take<double>(n.layout == FIGARO_COL_MAJOR ? n.ld * n.N : M * n.ld);
+    }
+    b.key[0] = a.take<uint64_t>(M);
+    b.key[1] = a.take<uint64_t>(M);
+    b.perm[0] = a.take<int32_t>(M);
+    b.perm[1] = a.take<int32_t>(M);
+    b.row_gid = a.take<int32_t>(M);
+    b.goff = a.take<int32_t>(M + 1);
+    b.gkey = a.take<uint64_t>(M);
+    b.g2p = a.take<int32_t>(M);
+    b.pgoff = a.take<int32_t>(M + 1);
+    b.pkey = a.take<uint64_t>(M);
+    b.sizes = a.take<int32_t>(4);
+    b.itmp = a.take<int32_t>(M);
+    b.scan_tmp_i = a.take<int32_t>(scan_tmp_elems(M));
+    b.scan_tmp_u = a.take<uint64_t>(scan_tmp_elems(M));
+    b.theta = a.take<uint64_t>(M);
+    b.full = a.take<uint64_t>(M);
+    b.phic = a.take<uint64_t>(M);
+    b.phid = a.take<uint64_t>(M);
+    b.phiu = a.take<uint64_t>(M);
+    b.theta_incl = a.take<uint64_t>(M);
+    b.sq_phic = a.take<double>(M);
+    b.hrow = a.take<double>(M);
+    b.q = a.take<int32_t>((int64_t)std::max(nch, 1) * M);
+    b.fac = a.take<double>(M * (1 + nch));
+    b.vw = a.take<double>(3 * M);
+    b.hf = a.take<double>(M);
+    b.heads = a.take<double>(M * std::max(n.N, 1));
+    b.tails = a.take<double>(M * std::max(n.N, 1));
+    b.tails32 = nullptr;
+    if (!n.leaf && !n.root) {
+      b.data2 = a.take<double>(M * n.N_sub);
+      b.gtails = a.take<double>(M * n.N_sub);
+    }
+    if (n.root) b.rootrows = a.take<double>(M * n.N_sub);
+    n.n_tiles = ht_tiles(M);
+    const int wide = std::max(std::max(n.N, n.N_sub), 1);
+    b.tflag = a.take<uint8_t>(n.n_tiles * wide);
+    b.tsum = a.take<double>(n.n_tiles * wide);
+    b.tcarry = a.take<double>(n.n_tiles * wide);
+    b.coldesc = a.take<int2>(std::max(n.N_sub, 1));
+  }
+  int64_t scratch = 0;
+  for (auto& blk : P.blocks) {
+    blk.tri[0] = a.take<double>(tsqr_tri_elems(blk));
+    blk.tri[1] = a.take<double>(tsqr_tri_elems(blk));
+    blk.cols = a.take<int>(blk.n);
+    scratch = std::max(scratch, tsqr_scratch_elems(blk, mixed));
+  }
+  P.tsqr_scratch = a.take<double>(scratch);
+  P.blocks_dev = a.take<TsqrBlock>((int64_t)P.blocks.size());
+  P.stack = a.take<double>((int64_t)P.stack_rows * P.N);
+  const int64_t NN = (int64_t)P.N * P.N;
+  P.Rtmp = a.take<double>(NN);
+  P.svdW = a.take<double>(NN);
+  P.svdV = a.take<double>(NN);
+  P.sig = a.take<double>(P.N);
+  P.Vtmp = a.take<double>(NN);
+  P.hostbuf_dev = a.take<double>(NN + P.N);
+}
+
+// ------------------------------------------------------------------ validation + planning
+static int build(figaro_plan_s& P, const figaro_join_tree* tree) {
+  const int r = tree->n_rel;
+  if (r < 1 || !tree->rels || !tree->parent) return fail(FIGARO_ERR_INVALID_ARG, "empty database");
+  P.nodes.resize(r);
+  int roots = 0;
+  for (int i = 0; i < r; ++i) {
+    const figaro_relation& R = tree->rels[i];
+    Node& n = P.nodes[i];
+    n.id = i;
+    n.parent = tree->parent[i];
+    if (n.parent < -1 || n.parent >= r || n.parent == i)
+      return fail(FIGARO_ERR_INVALID_TREE, "parent index out of range in relation " + std::to_string(i));
+    if (n.parent < 0) { ++roots; P.root = i; }
+    if (R.n_rows < 1 || R.n_rows > 0x7fffffffLL)
+      return fail(FIGARO_ERR_INVALID_ARG, "n_rows must be in [1, 2^31-1] (relation " + std::to_string(i) + ")");
+    if (R.n_keys < 0 || R.n_keys > kMaxKeys)
+      return fail(R.n_keys < 0 ? FIGARO_ERR_INVALID_ARG : FIGARO_ERR_UNSUPPORTED, "n_keys must be in [0, 8]");
+    if (R.n_data < 0) return fail(FIGARO_ERR_INVALID_ARG, "n_data < 0");
+    if (R.key_type != FIGARO_KEY_I64 && R.key_type != FIGARO_KEY_I32) return fail(FIGARO_ERR_INVALID_ARG, "key_type");
+    if (R.layout != FIGARO_COL_MAJOR && R.layout != FIGARO_ROW_MAJOR) return fail(FIGARO_ERR_INVALID_ARG, "layout");
+    if (R.n_keys > 0 && (!R.key_attr || !R.key_cols)) return fail(FIGARO_ERR_INVALID_ARG, "null key arrays");
+    if (R.n_data > 0 && !R.data) return fail(FIGARO_ERR_INVALID_ARG, "null data");
+    if (R.layout == FIGARO_COL_MAJOR ? R.ld < R.n_rows : R.ld < R.n_data)
+      return fail(FIGARO_ERR_INVALID_ARG, "leading dimension too small (relation " + std::to_string(i) + ")");
+    n.M = R.n_rows;
+    n.K = R.n_keys;
+    n.N = R.n_data;
+    n.key_type = R.key_type;
+    n.layout = R.layout;
+    n.ld = R.ld;
+    n.data = R.data;
+    for (int k = 0; k < n.K; ++k) {
+      if (R.key_attr[k] < 0) return fail(FIGARO_ERR_INVALID_ARG, "negative attribute id");
+      if (!R.key_cols[k]) return fail(FIGARO_ERR_INVALID_ARG, "null key column");
+      for (int kk = 0; kk < k; ++kk)
+        if (R.key_attr[kk] == R.key_attr[k]) return fail(FIGARO_ERR_INVALID_ARG, "repeated attribute in a relation");
+      n.key_attr.push_back(R.key_attr[k]);
+      n.key_ptr.push_back(R.key_cols[k]);
+    }
+    n.dkey.assign(n.K, nullptr);
+    P.input_cells += n.M * (n.N + n.K);
+    P.input_bytes += n.M * (8 * (int64_t)n.N + (n.key_type == FIGARO_KEY_I32 ? 4 : 8) * (int64_t)n.K);
+  }
+  if (roots != 1) return fail(FIGARO_ERR_INVALID_TREE, "the join tree must have exactly one root");
+  for (int i = 0; i < r; ++i)
+    if (P.nodes[i].parent >= 0) P.nodes[P.nodes[i].parent].children.push_back(i);
+  for (auto& n : P.nodes) {
+    if ((int)n.children.size() > kMaxChildren) return fail(FIGARO_ERR_UNSUPPORTED, "more than 8 children");
+    n.leaf = n.children.empty();
+    n.root = n.parent < 0;
+  }
+  // connectivity and acyclicity: a DFS from the root must reach every node once
+  {
+    std::vector<int> seen(r, 0), stack{P.root};
+    while (!stack.empty()) {
+      int u = stack.back();
+      stack.pop_back();
+      if (seen[u]++) return fail(FIGARO_ERR_INVALID_TREE, "parent[] has a cycle");
+      P.pre.push_back(u);
+      for (int c : P.nodes[u].children) stack.push_back(c);
+    }
+    for (int i = 0; i < r; ++i)
+      if (!seen[i]) return fail(FIGARO_ERR_INVALID_TREE, "parent[] is not connected");
+    // post-order: reverse of a pre-order that visits children after the parent works
+    // as long as every child precedes its parent, which the reverse guarantees.
+    P.post.assign(P.pre.rbegin(), P.pre.rend());
+  }
+  // attributes: at least two holders, holders connected in the tree (§2 join tree)
+  int max_attr = -1;
+  for (auto& n : P.nodes)
+    for (int a : n.key_attr) max_attr = std::max(max_attr, a);
+  P.amin.assign(max_attr + 1, 0);
+  P.abits.assign(max_attr + 1, 0);
+  for (int a = 0; a <= max_attr; ++a) {
+    int holders = 0, tops = 0;
+    for (auto& n : P.nodes) {
+      bool has = std::find(n.key_attr.begin(), n.key_attr.end(), a) != n.key_attr.end();
+      if (!has) continue;
+      ++holders;
+      bool parent_has = n.parent >= 0 && std::find(P.nodes[n.parent].key_attr.begin(),
+                                                   P.nodes[n.parent].key_attr.end(), a) !=
+                                             P.nodes[n.parent].key_attr.end();
+      if (!parent_has) ++tops;
+    }
+    if (holders == 1)
+      return fail(FIGARO_ERR_INVALID_TREE, "attribute " + std::to_string(a) + " occurs in one relation only");
+    if (holders > 1 && tops != 1)
+      return fail(FIGARO_ERR_INVALID_TREE, "relations holding attribute " + std::to_string(a) +
+                                               " are not connected in the join tree");
+  }
+  // columns of A[:, Y]
+  int off = 0;
+  for (auto& n : P.nodes) {
+    n.col_off = off;
+    off += n.N;
+  }
+  P.N = off;
+  if (P.N < 1 || P.N > 1024) return fail(FIGARO_ERR_UNSUPPORTED, "total data columns must be in [1, 1024]");
+  for (int i : P.post) {
+    Node& n = P.nodes[i];
+    std::vector<int> cols;
+    for (int c = 0; c < n.N; ++c) cols.push_back(n.col_off + c);
+    for (int c : n.children) cols.insert(cols.end(), P.nodes[c].sub_cols.begin(), P.nodes[c].sub_cols.end());
+    std::sort(cols.begin(), cols.end());
+    n.sub_cols = cols;
+    n.N_sub = (int)cols.size();
+    for (int gc : cols) {
+      if (gc >= n.col_off && gc < n.col_off + n.N) {
+        n.coldesc.push_back(make_int2(0, gc - n.col_off));
+        continue;
+      }
+      for (int jj = 0; jj < (int)n.children.size(); ++jj) {
+        const auto& sc = P.nodes[n.children[jj]].sub_cols;
+        auto it = std::find(sc.begin(), sc.end(), gc);
+        if (it != sc.end()) {
+          n.coldesc.push_back(make_int2(1 + jj, (int)(it - sc.begin())));
+          break;
+        }
+      }
+    }
+  }
+  return FIGARO_OK;
+}
+
+static int scan_key_ranges(figaro_plan_s& P) {
+  const int na = (int)P.amin.size();
+  std::vector<long long> lo(na, LLONG_MAX), hi(na, LLONG_MIN);
+  std::vector<std::pair<int, int>> cols;
+  for (auto& n : P.nodes)
+    for (int k = 0; k < n.K; ++k) cols.push_back({n.id, k});
+  if (cols.empty()) return FIGARO_OK;
+  if (P.opt.mem == FIGARO_MEM_HOST) {
+    for (auto [i, k] : cols) {
+      const Node& n = P.nodes[i];
+      int a = n.key_attr[k];
+      for (int64_t r = 0; r < n.M; ++r) {
+        long long v = n.key_type == FIGARO_KEY_I32 ? (long long)static_cast<const int32_t*>(n.key_ptr[k])[r]
+                                                   : static_cast<const long long*>(n.key_ptr[k])[r];
+        lo[a] = std::min(lo[a], v);
+        hi[a] = std::max(hi[a], v);
+      }
+    }
+  } else {
+    long long* d = nullptr;
+    FIG_CUDA(cudaMalloc(&d, 2 * sizeof(long long) * cols.size()));
+    std::vector<long long> init(2 * cols.size());
+    for (size_t c = 0; c < cols.size(); ++c) { init[2 * c] = LLONG_MAX; init[2 * c + 1] = LLONG_MIN; }
+    cudaError_t e = cudaMemcpyAsync(d, init.data(), init.size() * sizeof(long long), cudaMemcpyHostToDevice, P.st);
+    for (size_t c = 0; c < cols.size() && e == cudaSuccess; ++c) {
+      const Node& n = P.nodes[cols[c].first];
+      launch_minmax(n.key_ptr[cols[c].second], n.key_type, n.M, d + 2 * c, d + 2 * c + 1, P.st);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(init.data(), d, init.size() * sizeof(long long), cudaMemcpyDeviceToHost, P.st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(P.st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(FIGARO_ERR_CUDA, std::string("key range scan: ") + cudaGetErrorString(e));
+    for (size_t c = 0; c < cols.size(); ++c) {
+      int a = P.nodes[cols[c].first].key_attr[cols[c].second];
+      lo[a] = std::min(lo[a], init[2 * c]);
+      hi[a] = std::max(hi[a], init[2 * c + 1]);
+    }
+  }
+  for (int a = 0; a < na; ++a) {
+    if (lo[a] > hi[a]) continue;
+    P.amin[a] = lo[a];
+    P.abits[a] = bits_for((unsigned long long)(hi[a] - lo[a]));
+  }
+  // packing of every relation
+  for (auto& n : P.nodes) {
+    std::vector<int> xp, rest;
+    for (int a : n.key_attr) {
+      bool shared = false;
+      if (n.parent >= 0) {
+        const auto& pa = P.nodes[n.parent].key_attr;
+        shared = std::find(pa.begin(), pa.end(), a) != pa.end();
+      }
+      (shared ? xp : rest).push_back(a);
+    }
+    std::sort(xp.begin(), xp.end());
+    std::sort(rest.begin(), rest.end());
+    n.pack_attr = xp;
+    n.pack_attr.insert(n.pack_attr.end(), rest.begin(), rest.end());
+    int total = 0;
+    for (int a : n.pack_attr) total += P.abits[a];
+    if (total > 64)
+      return fail(FIGARO_ERR_UNSUPPORTED, "packed key of relation " + std::to_string(n.id) + " needs " +
+                                              std::to_string(total) + " bits (> 64)");
+    n.bits = total;
+    n.rest_bits = 0;
+    for (int a : rest) n.rest_bits += P.abits[a];
+    int cur = total;
+    n.shift.clear();
+    n.pack_col.clear();
+    for (int a : n.pack_attr) {
+      cur -= P.abits[a];
+      n.shift.push_back(cur);
+      n.pack_col.push_back((int)(std::find(n.key_attr.begin(), n.key_attr.end(), a) - n.key_attr.begin()));
+    }
+  }
+  return FIGARO_OK;
+}
+
+static int shift_of(const Node& n, int a) {
+  for (size_t k = 0; k < n.pack_attr.size(); ++k)
+    if (n.pack_attr[k] == a) return n.shift[k];
+  return -1;
+}
+
+static void make_links(figaro_plan_s& P) {
+  for (auto& n : P.nodes) {
+    for (int jj = 0; jj < (int)n.children.size(); ++jj) {
+      Node& c = P.nodes[n.children[jj]];
+      ChildLink& L = n.link[jj];
+      L = ChildLink{};
+      int na = 0;
+      for (int a : c.pack_attr) {
+        if (shift_of(c, a) < c.rest_bits) continue;   // not in the child's X_p
+        L.src_shift[na] = shift_of(n, a);
+        L.bits[na] = P.abits[a];
+        L.dst_shift[na] = shift_of(c, a) - c.rest_bits;
+        ++na;
+      }
+      L.n_attr = na;
+      L.pkey = c.b.pkey;
+      L.sizes = c.b.sizes;
+      L.phid = c.b.phid;
+      L.phiu = c.b.phiu;
+      L.q = n.b.q + (int64_t)jj * n.M;
+      L.data = c.leaf ? c.b.heads : c.b.data2;
+      L.ld = c.M;
+    }
+  }
+}
+
+static void make_blocks(figaro_plan_s& P) {
+  const bool mixed = P.opt.precision == FIGARO_PREC_MIXED;
+  P.blocks.clear();
+  P.stack_rows = 0;
+  for (auto& n : P.nodes) {
+    if (n.N > 0) {
+      TsqrBlock t{};
+      t.n = n.N;
+      t.kind = BLK_TAILS;
+      t.M = n.M;
+      t.bound = n.M;
+      tsqr_plan_block(t, mixed);
+      P.blocks.push_back(t);
+      P.stack_rows += t.n;
+    }
+    if (!n.leaf && !n.root && n.N_sub > 0) {
+      TsqrBlock t{};
+      t.n = n.N_sub;
+      t.kind = BLK_GEN;
+      t.M = n.M;
+      t.bound = n.M;
+      tsqr_plan_block(t, mixed);
+      P.blocks.push_back(t);
+      P.stack_rows += t.n;
+    }
+    if (n.root) {
+      TsqrBlock t{};
+      t.n = n.N_sub;
+      t.kind = BLK_ROOT;
+      t.M = n.M;
+      t.bound = n.M;
+      tsqr_plan_block(t, mixed);
+      P.blocks.push_back(t);
+      P.stack_rows += t.n;
+    }
+  }
+}
+
+// block pointers that depend on the arena
+static void bind_blocks(figaro_plan_s& P) {
+  size_t bi = 0;
+  for (auto& n : P.nodes) {
+    if (n.N > 0) {
+      P.blocks[bi].ptr = n.b.tails;
+      P.blocks[bi].ld = n.M;
+      P.blocks[bi].sizes = n.b.sizes;
+      ++bi;
+    }
+    if (!n.leaf && !n.root && n.N_sub > 0) {
+      P.blocks[bi].ptr = n.b.gtails;
+      P.blocks[bi].ld = n.M;
+      P.blocks[bi].sizes = n.b.sizes;
+      ++bi;
+    }
+    if (n.root) {
+      P.blocks[bi].ptr = n.b.rootrows;
+      P.blocks[bi].ld = n.M;
+      P.blocks[bi].sizes = n.b.sizes;
+      ++bi;
+    }
+  }
+}
+
+static std::vector<int> block_cols(const figaro_plan_s& P, size_t bi) {
+  size_t k = 0;
+  for (auto& n : P.nodes) {
+    if (n.N > 0) {
+      if (k++ == bi) {
+        std::vector<int> c;
+        for (int j = 0; j < n.N; ++j) c.push_back(n.col_off + j);
+        return c;
+      }
+    }
+    if (!n.leaf && !n.root && n.N_sub > 0)
+      if (k++ == bi) return n.sub_cols;
+    if (n.root)
+      if (k++ == bi) return n.sub_cols;
+  }
+  return {};
+}
+
+// ------------------------------------------------------------------ per-call pipeline
+struct StageClock {
+  figaro_plan_s& P;
+  int64_t l0 = 0;
+  int s = -1;
+  explicit StageClock(figaro_plan_s& p) : P(p) {}
+  void start(int stage) {
+    s = stage;
+    l0 = P.launches;
+    if (P.opt.stage_timing) cudaEventRecord(P.ev[stage], P.st);
+  }
+  void stop() {
+    if (P.opt.stage_timing) cudaEventRecord(P.ev[s + 1], P.st);
+    P.stage_launch[s] += P.launches - l0;
+  }
+};
+
+static int run_r(figaro_plan_s& P, double* R, int64_t ldr) {
+  cudaStream_t st = P.st;
+  const bool mixed = P.opt.precision == FIGARO_PREC_MIXED;
+  P.launches = 0;
+  FIG_CUDA(cudaMemsetAsync(P.err_dev, 0, sizeof(int), st));
+  if (P.opt.mem == FIGARO_MEM_HOST) {
+    for (auto& n : P.nodes) {
+      for (int k = 0; k < n.K; ++k)
+        FIG_CUDA(cudaMemcpyAsync(n.dkey[k], n.key_ptr[k], n.M * (n.key_type == FIGARO_KEY_I32 ? 4 : 8),
+                                 cudaMemcpyHostToDevice, st));
+      if (n.N > 0) {
+        const int64_t elems = n.layout == FIGARO_COL_MAJOR ? n.ld * (n.N - 1) + n.M : n.ld * (n.M - 1) + n.N;
+        FIG_CUDA(cudaMemcpyAsync(n.ddata, n.data, elems * sizeof(double), cudaMemcpyHostToDevice, st));
+      }
+    }
+  }
+  StageClock clk(P);
+  // ---- stage 0: pack + sort
+  clk.start(0);
+  for (auto& n : P.nodes) {
+    PackParams pp{};
+    pp.n_keys = (int)n.pack_attr.size();
+    pp.key_type = n.key_type;
+    for (int k = 0; k < pp.n_keys; ++k) {
+      const int col = n.pack_col[k];
+      pp.cols[k] = P.opt.mem == FIGARO_MEM_HOST ? n.dkey[col] : n.key_ptr[col];
+      pp.kmin[k] = P.amin[n.pack_attr[k]];
+      pp.shift[k] = n.shift[k];
+      pp.bits[k] = P.abits[n.pack_attr[k]];
+    }
+    const bool sort = !P.opt.presorted && n.bits > 0;
+    launch_pack(pp, n.M, n.b.key[0], sort ? n.b.perm[0] : nullptr, P.err_dev, st, &P.launches);
+    if (sort) {
+      int cur = radix_sort(n.b.key, n.b.perm, n.M, n.bits, P.radix_hist, P.radix_scan_tmp, st, &P.launches);
+      n.b.skey = n.b.key[cur];
+      n.b.sperm = n.b.perm[cur];
+    } else {
+      if (P.opt.presorted) check_sorted(n.b.key[0], n.M, P.err_dev, st, &P.launches);
+      n.b.skey = n.b.key[0];
+      n.b.sperm = nullptr;
+    }
+  }
+  clk.stop();
+  // ---- stage 1: segmentation
+  clk.start(1);
+  for (auto& n : P.nodes) segment(n.b, n.M, n.rest_bits, st, &P.launches);
+  clk.stop();
+  // ---- stage 2: counts (Alg. 3)
+  clk.start(2);
+  make_links(P);
+  auto count_params = [&](Node& n) {
+    CountParams c{};
+    c.n_child = (int)n.children.size();
+    for (int j = 0; j < c.n_child; ++j) c.ch[j] = n.link[j];
+    c.is_root = n.root;
+    c.require_reduced = P.opt.require_reduced;
+    c.M = n.M;
+    c.gkey = n.b.gkey;
+    c.goff = n.b.goff;
+    c.g2p = n.b.g2p;
+    c.pgoff = n.b.pgoff;
+    c.sizes = n.b.sizes;
+    c.theta = n.b.theta;
+    c.full = n.b.full;
+    c.phic = n.b.phic;
+    c.phid = n.b.phid;
+    c.phiu = n.b.phiu;
+    c.theta_incl = n.b.theta_incl;
+    c.sq_phic = n.b.sq_phic;
+    c.hrow = n.b.hrow;
+    c.fac = n.b.fac;
+    c.vw = n.b.vw;
+    c.hf = n.b.hf;
+    return c;
+  };
+  for (auto& n : P.nodes) {
+    FIG_CUDA(cudaMemsetAsync(n.b.phid, 0, sizeof(uint64_t) * n.M, st));
+    FIG_CUDA(cudaMemsetAsync(n.b.phiu, 0, sizeof(uint64_t) * n.M, st));
+  }
+  for (int i : P.post) counts_pass1(count_params(P.nodes[i]), st, P.err_dev, &P.launches);
+  for (int i : P.pre) {
+    Node& n = P.nodes[i];
+    counts_pass2(count_params(n), st, P.err_dev, &P.launches);
+    for (int j = 0; j < (int)n.children.size(); ++j)
+      counts_finalize_child(n.link[j], P.nodes[n.children[j]].M, st, &P.launches);
+  }
+  for (auto& n : P.nodes) {
+    if (n.leaf && !n.root) continue;
+    if (!n.root) {
+      ScanSrc src{SCAN_PLAIN_U64, n.b.theta, 0};
+      scan_inclusive<uint64_t>(src, n.b.theta_incl, n.M, n.b.sizes, n.b.scan_tmp_u, st, &P.launches);
+    }
+    join_prep(count_params(n), st, &P.launches);
+  }
+  clk.stop();
+  // ---- stage 3: heads and tails of every relation
+  clk.start(3);
+  for (auto& n : P.nodes) {
+    LeafParams lp{};
+    lp.M = n.M;
+    lp.N = n.N;
+    lp.data = P.opt.mem == FIGARO_MEM_HOST ? n.ddata : n.data;
+    lp.rs = n.layout == FIGARO_COL_MAJOR ? 1 : n.ld;
+    lp.cs = n.layout == FIGARO_COL_MAJOR ? n.ld : 1;
+    lp.perm = n.b.sperm;
+    lp.row_gid = n.b.row_gid;
+    lp.goff = n.b.goff;
+    lp.sq_phic = n.b.sq_phic;
+    lp.hrow = n.b.hrow;
+    lp.beta = P.beta;
+    lp.beta_len = P.beta_len;
+    lp.tails = n.b.tails;
+    lp.ldt = n.M;
+    lp.heads = n.b.heads;
+    lp.ldh = n.M;
+    lp.tflag = n.b.tflag;
+    lp.tsum = n.b.tsum;
+    lp.tcarry = n.b.tcarry;
+    lp.n_tiles = n.n_tiles;
+    leaf_heads_tails(lp, st, &P.launches);
+  }
+  clk.stop();
+  // ---- stage 4: join children, project away, root rows (post-order)
+  clk.start(4);
+  for (int i : P.post) {
+    Node& n = P.nodes[i];
+    if (n.leaf && !n.root) continue;
+    GenParams gp{};
+    gp.N = n.N_sub;
+    gp.n_child = (int)n.children.size();
+    gp.M = n.M;
+    gp.sizes = n.b.sizes;
+    gp.g2p = n.b.g2p;
+    gp.pgoff = n.b.pgoff;
+    gp.heads = n.b.heads;
+    gp.ldh = n.M;
+    gp.fac = n.b.fac;
+    gp.vw = n.b.vw;
+    gp.hf = n.b.hf;
+    gp.q = n.b.q;
+    for (int j = 0; j < gp.n_child; ++j) {
+      gp.cdata[j] = n.link[j].data;
+      gp.cld[j] = n.link[j].ld;
+    }
+    gp.coldesc = n.b.coldesc;
+    gp.gtails = n.b.gtails;
+    gp.data2 = n.b.data2;
+    gp.rootrows = n.b.rootrows;
+    gp.tflag = n.b.tflag;
+    gp.tsum = n.b.tsum;
+    gp.tcarry = n.b.tcarry;
+    gp.n_tiles = n.n_tiles;
+    gp.is_root = n.root;
+    if (gp.N > 0) gen_heads_tails(gp, st, &P.launches);
+  }
+  clk.stop();
+  // ---- stage 5: TSQR leaves
+  clk.start(5);
+  for (auto& b : P.blocks) tsqr_leaf(b, mixed, P.tsqr_scratch, st, &P.launches);
+  clk.stop();
+  // ---- stage 6: TSQR tree + final
+  clk.start(6);
+  for (auto& b : P.blocks) tsqr_reduce(b, P.tsqr_scratch, st, &P.launches);
+  tsqr_final(P.blocks_dev, (int)P.blocks.size(), P.stack_rows, P.N, P.stack, R, ldr, st, &P.launches);
+  clk.stop();
+  FIG_CUDA(cudaGetLastError());
+  return FIGARO_OK;
+}
+
+static int finish(figaro_plan_s& P, int stages_used) {
+  FIG_CUDA(cudaMemcpyAsync(P.err_host, P.err_dev, sizeof(int), cudaMemcpyDeviceToHost, P.st));
+  for (size_t i = 0; i < P.nodes.size(); ++i)
+    FIG_CUDA(cudaMemcpyAsync(P.err_host + 4 + 4 * i, P.nodes[i].b.sizes, 4 * sizeof(int32_t),
+                             cudaMemcpyDeviceToHost, P.st));
+  FIG_CUDA(cudaStreamSynchronize(P.st));
+  FIG_CUDA(cudaGetLastError());
+  if (P.opt.stage_timing) {
+    for (int s = 0; s < stages_used; ++s) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, P.ev[s], P.ev[s + 1]) == cudaSuccess) P.stage_ms[s] += ms;
+    }
+  }
+  // bookkeeping for figaro_plan_get_info: R0 rows and TSQR leaf flops of this call
+  P.r0_rows = 0;
+  P.leaf_flops = 0.0;
+  for (size_t i = 0; i < P.nodes.size(); ++i) {
+    const Node& n = P.nodes[i];
+    const int64_t G = P.err_host[4 + 4 * i], Pg = P.err_host[4 + 4 * i + 1];
+    if (n.N > 0) { P.r0_rows += n.M - G; P.leaf_flops += tsqr_leaf_flops(n.M - G, n.N); }
+    if (!n.leaf && !n.root && n.N_sub > 0) { P.r0_rows += G - Pg; P.leaf_flops += tsqr_leaf_flops(G - Pg, n.N_sub); }
+    if (n.root) { P.r0_rows += G; P.leaf_flops += tsqr_leaf_flops(G, n.N_sub); }
+  }
+  const int e = *P.err_host;
+  if (e != 0) return fail(e, std::string("device reported: ") + figaro_error_string(e));
+  return FIGARO_OK;
+}
+
+}  // namespace fig
+
+using namespace fig;
+
+extern "C" {
+
+void figaro_default_options(figaro_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->precision = FIGARO_PREC_FP64;
+  opt->mem = FIGARO_MEM_DEVICE;
+}
+
+const char* figaro_error_string(int s) {
+  switch (s) {
+    case FIGARO_OK: return "FIGARO_OK";
+    case FIGARO_ERR_INVALID_ARG: return "FIGARO_ERR_INVALID_ARG";
+    case FIGARO_ERR_INVALID_TREE: return "FIGARO_ERR_INVALID_TREE";
+    case FIGARO_ERR_NOT_REDUCED: return "FIGARO_ERR_NOT_REDUCED";
+    case FIGARO_ERR_OVERFLOW: return "FIGARO_ERR_OVERFLOW";
+    case FIGARO_ERR_NOMEM: return "FIGARO_ERR_NOMEM";
+    case FIGARO_ERR_TIMEOUT: return "FIGARO_ERR_TIMEOUT";
+    case FIGARO_ERR_CUDA: return "FIGARO_ERR_CUDA";
+    case FIGARO_ERR_KEY_RANGE: return "FIGARO_ERR_KEY_RANGE";
+    case FIGARO_ERR_NOT_SORTED: return "FIGARO_ERR_NOT_SORTED";
+    case FIGARO_ERR_UNSUPPORTED: return "FIGARO_ERR_UNSUPPORTED";
+    default: return "FIGARO_ERR_UNKNOWN";
+  }
+}
+
+const char* figaro_last_error(void) { return g_last_error.c_str(); }
+
+int figaro_plan_destroy(figaro_plan_t p) {
+  if (!p) return FIGARO_OK;
+  if (p->arena) cudaStreamSynchronize(p->st);
+  for (auto& e : p->ev)
+    if (e) cudaEventDestroy(e);
+  if (p->err_host) cudaFreeHost(p->err_host);
+  if (p->arena) cudaFree(p->arena);
+  delete p;
+  return FIGARO_OK;
+}
+
+int figaro_plan(const figaro_join_tree* tree, const figaro_options* opt, void* stream, figaro_plan_t* out) {
+  g_last_error.clear();
+  if (!out) return fail(FIGARO_ERR_INVALID_ARG, "out is null");
+  *out = nullptr;
+  if (!tree) return fail(FIGARO_ERR_INVALID_ARG, "tree is null");
+  auto* P = new (std::nothrow) figaro_plan_s();
+  if (!P) return fail(FIGARO_ERR_NOMEM, "host allocation");
+  if (opt) P->opt = *opt; else figaro_default_options(&P->opt);
+  if (P->opt.precision != FIGARO_PREC_FP64 && P->opt.precision != FIGARO_PREC_MIXED) {
+    delete P;
+    return fail(FIGARO_ERR_INVALID_ARG, "precision");
+  }
+  if (P->opt.mem != FIGARO_MEM_DEVICE && P->opt.mem != FIGARO_MEM_HOST) {
+    delete P;
+    return fail(FIGARO_ERR_INVALID_ARG, "mem");
+  }
+  P->st = static_cast<cudaStream_t>(stream);
+  int rc = build(*P, tree);
+  if (rc != FIGARO_OK) { delete P; return rc; }
+  if (cudaGetDevice(&P->device) != cudaSuccess) {
+    delete P;
+    return fail(FIGARO_ERR_CUDA, "no CUDA device");
+  }
+  rc = scan_key_ranges(*P);
+  if (rc != FIGARO_OK) { delete P; return rc; }
+  make_blocks(*P);
+  Arena measure;
+  layout(*P, measure);
+  P->arena_bytes = measure.off + 256;
+  if (cudaMalloc(&P->arena, P->arena_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    P->arena = nullptr;
+    figaro_plan_destroy(P);
+    return fail(FIGARO_ERR_NOMEM, "device workspace of " + std::to_string(P->arena_bytes) + " bytes");
+  }
+  Arena real;
+  real.base = P->arena;
+  layout(*P, real);
+  bind_blocks(*P);
+  auto bail = [&](cudaError_t e, const char* what) {
+    figaro_plan_destroy(P);
+    return fail(FIGARO_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  };
+  cudaError_t e = cudaMallocHost(&P->err_host, sizeof(int) * (4 + 4 * P->nodes.size()));
+  if (e != cudaSuccess) return bail(e, "cudaMallocHost");
+  for (auto& ev : P->ev) {
+    e = cudaEventCreate(&ev);
+    if (e != cudaSuccess) return bail(e, "cudaEventCreate");
+  }
+  // static tables: column descriptors, block column maps, block list, beta table
+  for (auto& n : P->nodes)
+    if (!n.coldesc.empty()) {
+      e = cudaMemcpyAsync(n.b.coldesc, n.coldesc.data(), n.coldesc.size() * sizeof(int2), cudaMemcpyHostToDevice, P->st);
+      if (e != cudaSuccess) return bail(e, "upload column map");
+    }
+  std::vector<std::vector<int>> cols(P->blocks.size());
+  for (size_t bi = 0; bi < P->blocks.size(); ++bi) {
+    cols[bi] = block_cols(*P, bi);
+    e = cudaMemcpyAsync(const_cast<int*>(P->blocks[bi].cols), cols[bi].data(), cols[bi].size() * sizeof(int),
+                        cudaMemcpyHostToDevice, P->st);
+    if (e != cudaSuccess) return bail(e, "upload block columns");
+  }
+  e = cudaMemcpyAsync(P->blocks_dev, P->blocks.data(), P->blocks.size() * sizeof(TsqrBlock), cudaMemcpyHostToDevice,
+                      P->st);
+  if (e != cudaSuccess) return bail(e, "upload blocks");
+  beta_table(P->beta, P->beta_len, P->st);
+  e = cudaStreamSynchronize(P->st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return bail(e, "plan setup");
+  *out = P;
+  return FIGARO_OK;
+}
+
+int figaro_qr_r(figaro_plan_t p, double* R, int64_t ldr) {
+  g_last_error.clear();
+  if (!p || !R) return fail(FIGARO_ERR_INVALID_ARG, "null plan or R");
+  if (ldr < p->N) return fail(FIGARO_ERR_INVALID_ARG, "ldr < N");
+  const bool host = p->opt.mem == FIGARO_MEM_HOST;
+  double* Rd = host ? p->Rtmp : R;
+  int64_t ld = host ? p->N : ldr;
+  int rc = run_r(*p, Rd, ld);
+  if (rc != FIGARO_OK) return rc;
+  if (host)
+    FIG_CUDA(cudaMemcpy2DAsync(R, ldr * sizeof(double), Rd, ld * sizeof(double), p->N * sizeof(double), p->N,
+                               cudaMemcpyDeviceToHost, p->st));
+  return finish(*p, 7);
+}
+
+static int run_svd(figaro_plan_s& P, double* R_out) {
+  int rc = run_r(P, P.Rtmp, P.N);
+  if (rc != FIGARO_OK) return rc;
+  StageClock clk(P);
+  clk.start(7);
+  jacobi_svd(P.Rtmp, P.N, P.N, P.svdW, P.svdV, P.sig, P.Vtmp, P.err_dev, P.st, &P.launches);
+  clk.stop();
+  if (R_out) {
+    const bool host = P.opt.mem == FIGARO_MEM_HOST;
+    FIG_CUDA(cudaMemcpyAsync(R_out, P.Rtmp, (size_t)P.N * P.N * sizeof(double),
+                             host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, P.st));
+  }
+  return FIGARO_OK;
+}
+
+int figaro_svd(figaro_plan_t p, double* sigma, double* V, double* R) {
+  g_last_error.clear();
+  if (!p || !sigma || !V) return fail(FIGARO_ERR_INVALID_ARG, "null argument");
+  int rc = run_svd(*p, R);
+  if (rc != FIGARO_OK) return rc;
+  const cudaMemcpyKind kind = p->opt.mem == FIGARO_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  FIG_CUDA(cudaMemcpyAsync(sigma, p->sig, p->N * sizeof(double), kind, p->st));
+  FIG_CUDA(cudaMemcpyAsync(V, p->Vtmp, (size_t)p->N * p->N * sizeof(double), kind, p->st));
+  return finish(*p, 8);
+}
+
+int figaro_pca(figaro_plan_t p, int32_t k, double* components, double* eigvals) {
+  g_last_error.clear();
+  if (!p || !components || !eigvals) return fail(FIGARO_ERR_INVALID_ARG, "null argument");
+  if (k < 1 || k > p->N) return fail(FIGARO_ERR_INVALID_ARG, "k must be in [1, N]");
+  int rc = run_svd(*p, nullptr);
+  if (rc != FIGARO_OK) return rc;
+  const bool host = p->opt.mem == FIGARO_MEM_HOST;
+  const cudaMemcpyKind kind = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  FIG_CUDA(cudaMemcpy2DAsync(components, k * sizeof(double), p->Vtmp, p->N * sizeof(double), k * sizeof(double), p->N,
+                             kind, p->st));
+  double* ev = host ? p->hostbuf_dev : eigvals;
+  square_values(p->sig, ev, k, p->st, &p->launches);
+  if (host) FIG_CUDA(cudaMemcpyAsync(eigvals, ev, k * sizeof(double), cudaMemcpyDeviceToHost, p->st));
+  return finish(*p, 8);
+}
+
+int figaro_plan_get_info(figaro_plan_t p, figaro_plan_info* info) {
+  if (!p || !info) return fail(FIGARO_ERR_INVALID_ARG, "null argument");
+  info->n_rel = (int32_t)p->nodes.size();
+  info->n_cols = p->N;
+  info->input_cells = p->input_cells;
+  info->input_bytes = p->input_bytes;
+  info->workspace_bytes = (int64_t)p->arena_bytes;
+  info->r0_rows = p->r0_rows;
+  info->launches = p->launches;
+  info->tsqr_leaf_flops = p->leaf_flops;
+  return FIGARO_OK;
+}
+
+int figaro_stage_times(figaro_plan_t p, double* ms, int64_t* counts, int32_t n) {
+  if (!p) return -FIGARO_ERR_INVALID_ARG;
+  for (int s = 0; s < n && s < kStages; ++s) {
+    if (ms) ms[s] = p->stage_ms[s];
+    if (counts) counts[s] = p->stage_launch[s];
+  }
+  return kStages;
+}
+
+int figaro_reset_stage_times(figaro_plan_t p) {
+  if (!p) return FIGARO_ERR_INVALID_ARG;
+  for (int s = 0; s < kStages; ++s) {
+    p->stage_ms[s] = 0.0;
+    p->stage_launch[s] = 0;
+  }
+  return FIGARO_OK;
+}
+
+int64_t figaro_debug_read(figaro_plan_t p, int32_t rel, int32_t what, void* dst, int64_t bytes) {
+  if (!p || rel < 0 || rel >= (int)p->nodes.size()) return -FIGARO_ERR_INVALID_ARG;
+  const Node& n = p->nodes[rel];
+  int32_t sz[4] = {0, 0, 0, 0};
+  if (cudaStreamSynchronize(p->st) != cudaSuccess ||
+      cudaMemcpy(sz, n.b.sizes, sizeof(sz), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return -FIGARO_ERR_CUDA;
+  const int64_t G = sz[0], Pg = sz[1];
+  auto copy2d = [&](const void* src, int64_t rows, int64_t cols, int64_t ld, size_t esz) -> int64_t {
+    const int64_t need = rows * cols * (int64_t)esz;
+    if (dst && bytes >= need && need > 0)
+      if (cudaMemcpy2D(dst, rows * esz, src, ld * esz, rows * esz, cols, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return -FIGARO_ERR_CUDA;
+    return need;
+  };
+  switch (what) {
+    case FIGARO_DBG_SIZES: {
+      int64_t v[8] = {n.M, G, Pg, n.M - G, (!n.leaf && !n.root) ? G - Pg : 0, n.root ? G : 0, n.K, n.N_sub};
+      if (dst && bytes >= (int64_t)sizeof(v)) std::memcpy(dst, v, sizeof(v));
+      return sizeof(v);
+    }
+    case FIGARO_DBG_PERM: {
+      if (!n.b.sperm) {   // identity
+        if (dst && bytes >= n.M * 4)
+          for (int64_t r = 0; r < n.M; ++r) static_cast<int32_t*>(dst)[r] = (int32_t)r;
+        return n.M * 4;
+      }
+      return copy2d(n.b.sperm, n.M, 1, n.M, 4);
+    }
+    case FIGARO_DBG_GROUP_OFF: return copy2d(n.b.goff, G + 1, 1, G + 1, 4);
+    case FIGARO_DBG_COUNTS: {
+      const int64_t need = 4 * G * 8;
+      if (dst && bytes >= need) {
+        std::vector<int32_t> off(G + 1);
+        std::vector<uint64_t> th(G), fu(G), ci(G);
+        if (cudaMemcpy(off.data(), n.b.goff, (G + 1) * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(th.data(), n.b.theta, G * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(fu.data(), n.b.full, G * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(ci.data(), n.b.phic, G * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+          return -FIGARO_ERR_CUDA;
+        uint64_t* o = static_cast<uint64_t*>(dst);
+        for (int64_t g = 0; g < G; ++g) {
+          o[4 * g] = (uint64_t)(off[g + 1] - off[g]);
+          o[4 * g + 1] = th[g];
+          o[4 * g + 2] = fu[g];
+          o[4 * g + 3] = ci[g];
+        }
+      }
+      return need;
+    }
+    case FIGARO_DBG_PCOUNTS: {
+      const int64_t need = 2 * Pg * 8;
+      if (dst && bytes >= need) {
+        std::vector<uint64_t> d(Pg), u(Pg);
+        if (cudaMemcpy(d.data(), n.b.phid, Pg * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(u.data(), n.b.phiu, Pg * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+          return -FIGARO_ERR_CUDA;
+        uint64_t* o = static_cast<uint64_t*>(dst);
+        for (int64_t q = 0; q < Pg; ++q) { o[2 * q] = d[q]; o[2 * q + 1] = u[q]; }
+      }
+      return need;
+    }
+    case FIGARO_DBG_TAILS: return copy2d(n.b.tails, n.M - G, n.N, n.M, 8);
+    case FIGARO_DBG_HEADS: return copy2d(n.b.heads, G, n.N, n.M, 8);
+    case FIGARO_DBG_GEN_TAILS:
+      if (n.leaf || n.root) return 0;
+      return copy2d(n.b.gtails, G - Pg, n.N_sub, n.M, 8);
+    case FIGARO_DBG_DATA:
+      if (n.leaf || n.root) return 0;
+      return copy2d(n.b.data2, Pg, n.N_sub, n.M, 8);
+    case FIGARO_DBG_ROOT_ROWS:
+      if (!n.root) return 0;
+      return copy2d(n.b.rootrows, G, n.N_sub, n.M, 8);
+    default: return -FIGARO_ERR_INVALID_ARG;
+  }
+}
+
+}  // extern "C"

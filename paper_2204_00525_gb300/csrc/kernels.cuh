@@ -1,0 +1,208 @@
+// Kernel parameter structs and launcher declarations (internal).
+#pragma once
+
+#include "common.cuh"
+
+namespace fig {
+
+// ------------------------------------------------------------------ keys.cu
+struct PackParams {
+  int n_keys;
+  int key_type;
+  const void* cols[kMaxKeys];   // key columns in packing order
+  long long kmin[kMaxKeys];
+  int shift[kMaxKeys];
+  int bits[kMaxKeys];
+};
+
+// Device buffers of one relation (node of the join tree).  Sizes in brackets are
+// allocation bounds; G (groups of X_i) and P (groups of X_p) live in sizes[0..1].
+struct NodeBuf {
+  uint64_t* key[2];     // [M] packed keys (ping-pong for the sort)
+  int32_t* perm[2];     // [M] permutation (ping-pong)
+  uint64_t* skey;       // sorted keys (points into key[])
+  int32_t* sperm;       // sorted permutation (points into perm[]), null if identity
+  int32_t* row_gid;     // [M] group of every sorted row
+  int32_t* goff;        // [M+1] group offsets
+  uint64_t* gkey;       // [M] group keys
+  int32_t* g2p;         // [M] parent group of every group
+  int32_t* pgoff;       // [M+1] parent-group offsets (in groups)
+  uint64_t* pkey;       // [M] parent-group keys (X_p part)
+  int32_t* sizes;       // [4] G, P
+  int32_t* itmp;        // [M] scan output scratch
+  int32_t* scan_tmp_i;  // scan tile sums
+  uint64_t* scan_tmp_u; // scan tile sums (uint64)
+  // counts (§5)
+  uint64_t* theta;      // [M] Theta_down per group
+  uint64_t* full;       // [M] full_join_size per group
+  uint64_t* phic;       // [M] Phi_circ per group
+  uint64_t* phid;       // [M] Phi_down per parent group
+  uint64_t* phiu;       // [M] Phi_up per parent group
+  uint64_t* theta_incl; // [M] inclusive prefix of theta over groups
+  double* sq_phic;      // [M] sqrt(Phi_circ) per group
+  double* hrow;         // [M] 1/sqrt(rows) per group
+  int32_t* q;           // [n_children * M] index of x_ij among the child's parent groups
+  // generalized head/tail inputs (internal nodes)
+  double* fac;          // [M * (1 + n_children)] scale factors per group
+  double* vw;           // [M * 3] v, W, gamma per group
+  double* hf;           // [M] 1 / sqrt(Phi_down) per parent group
+  // outputs
+  double* heads;        // [M x N_i] col-major, ld M
+  double* tails;        // [M x N_i] col-major, ld M  (rows M - G used)
+  float* tails32;       // optional float copy for the mixed TSQR
+  double* data2;        // [M x N_sub] col-major: generalized heads for the parent
+  double* gtails;       // [M x N_sub] col-major: generalized tails
+  double* rootrows;     // [M x N] col-major (root only)
+  // scan tile aggregates
+  uint8_t* tflag;       // [n_tiles * max(N_i, N_sub)]
+  double* tsum;
+  double* tcarry;
+  int2* coldesc;        // [N_sub] (source kind, source column) for the join
+};
+
+void launch_minmax(const void* col, int key_type, int64_t n, long long* dmin, long long* dmax,
+                   cudaStream_t st);
+void launch_pack(const PackParams& p, int64_t n, uint64_t* key, int32_t* perm, int* err,
+                 cudaStream_t st, int64_t* launches);
+int64_t radix_tiles(int64_t n);
+int radix_sort(uint64_t* key[2], int32_t* perm[2], int64_t n, int bits, int32_t* hist, int32_t* scan_tmp,
+               cudaStream_t st, int64_t* launches);
+void segment(NodeBuf& b, int64_t n, int rest_bits, cudaStream_t st, int64_t* launches);
+void check_sorted(const uint64_t* key, int64_t n, int* err, cudaStream_t st, int64_t* launches);
+
+// ------------------------------------------------------------------ counts.cu
+struct ChildLink {
+  int n_attr;
+  int src_shift[kMaxKeys];   // field position in the parent's packed key
+  int bits[kMaxKeys];
+  int dst_shift[kMaxKeys];   // field position in the child's X_p key
+  const uint64_t* pkey;      // child's parent-group keys [P_c], strictly increasing
+  const int32_t* sizes;      // child's sizes (P_c = sizes[1])
+  const uint64_t* phid;      // child's Phi_down [P_c]
+  uint64_t* phiu;            // child's Phi_up [P_c] (accumulated, then divided)
+  int32_t* q;                // [G_i] out
+  const double* data;        // child's table of heads passed up (leaf: heads, else data2)
+  int64_t ld;                // its leading dimension
+};
+
+struct CountParams {
+  int n_child;
+  ChildLink ch[kMaxChildren];
+  int is_root;
+  int require_reduced;
+  int64_t M;
+  const uint64_t* gkey;
+  const int32_t* goff;
+  const int32_t* g2p;
+  const int32_t* pgoff;
+  const int32_t* sizes;
+  uint64_t* theta;
+  uint64_t* full;
+  uint64_t* phic;
+  uint64_t* phid;
+  const uint64_t* phiu;
+  const uint64_t* theta_incl;
+  double* sq_phic;
+  double* hrow;
+  double* fac;
+  double* vw;
+  double* hf;
+};
+
+void counts_pass1(const CountParams& p, cudaStream_t st, int* err, int64_t* launches);
+void counts_pass2(const CountParams& p, cudaStream_t st, int* err, int64_t* launches);
+void counts_finalize_child(const ChildLink& c, int64_t bound, cudaStream_t st, int64_t* launches);
+void join_prep(const CountParams& p, cudaStream_t st, int64_t* launches);
+
+// ------------------------------------------------------------------ heads.cu
+constexpr int kHtItems = 8;
+constexpr int kHtTile = 32 * kHtItems;   // elements per warp tile
+inline int64_t ht_tiles(int64_t n) { return (n + kHtTile - 1) / kHtTile; }
+
+struct LeafParams {
+  int64_t M;
+  int N;
+  const double* data;
+  int64_t rs, cs;            // element (input row r, column c) at data[r * rs + c * cs]
+  const int32_t* perm;       // sorted position -> input row; null means identity
+  const int32_t* row_gid;
+  const int32_t* goff;
+  const double* sq_phic;
+  const double* hrow;
+  const double* beta;        // beta[p] = 1 / sqrt(p (p + 1))
+  int64_t beta_len;
+  double* tails;
+  int64_t ldt;
+  double* heads;
+  int64_t ldh;
+  uint8_t* tflag;
+  double* tsum;
+  double* tcarry;
+  int64_t n_tiles;
+};
+
+struct GenParams {
+  int N;                     // N_sub
+  int n_child;
+  int64_t M;                 // allocation bound of groups
+  const int32_t* sizes;      // G at [0], P at [1]
+  const int32_t* g2p;
+  const int32_t* pgoff;
+  const double* heads;       // own heads [G x N_i], ld ldh
+  int64_t ldh;
+  const double* fac;
+  const double* vw;
+  const double* hf;
+  const int32_t* q;          // [n_child * M]
+  const double* cdata[kMaxChildren];
+  int64_t cld[kMaxChildren];
+  const int2* coldesc;
+  double* gtails;            // [G - P x N_sub], ld M
+  double* data2;             // [P x N_sub], ld M
+  double* rootrows;          // root only: [G x N], ld M
+  uint8_t* tflag;
+  double* tsum;
+  double* tcarry;
+  int64_t n_tiles;
+  int is_root;
+};
+
+void beta_table(double* beta, int64_t len, cudaStream_t st);
+void leaf_heads_tails(const LeafParams& p, cudaStream_t st, int64_t* launches);
+void gen_heads_tails(const GenParams& p, cudaStream_t st, int64_t* launches);
+
+// ------------------------------------------------------------------ tsqr.cu
+enum BlockKind : int { BLK_TAILS = 0, BLK_GEN = 1, BLK_ROOT = 2 };
+
+struct TsqrBlock {
+  const double* ptr;         // col-major, leading dimension ld
+  int64_t ld;
+  int n;                     // columns
+  int kind;
+  int64_t M;
+  const int32_t* sizes;      // rows = M - G (tails), G - P (gen), G (root)
+  int64_t bound;             // allocation bound of rows
+  int tile;                  // leaf tile rows
+  int fan;                   // triangles merged per reduce tile
+  int levels;                // reduce levels after the leaf
+  double* tri[2];            // ping-pong triangle buffers [bound tiles x n x n]
+  int top;                   // buffer holding the last level
+  const int* cols;           // device [n]: global column of each block column
+};
+
+void tsqr_plan_block(TsqrBlock& b, bool mixed);
+int64_t tsqr_tri_elems(const TsqrBlock& b);
+int64_t tsqr_scratch_elems(const TsqrBlock& b, bool mixed);
+void tsqr_leaf(const TsqrBlock& b, bool mixed, void* scratch, cudaStream_t st, int64_t* launches);
+void tsqr_reduce(TsqrBlock& b, void* scratch, cudaStream_t st, int64_t* launches);
+void tsqr_final(const TsqrBlock* blocks_dev, int n_blocks, int stack_rows, int N, double* stack,
+                double* R, int64_t ldr, cudaStream_t st, int64_t* launches);
+double tsqr_leaf_flops(int64_t rows, int n);
+
+// ------------------------------------------------------------------ svd.cu
+size_t jacobi_smem(int N);
+void jacobi_svd(const double* R, int64_t ldr, int N, double* W, double* V, double* sigma,
+                double* Vout, int* err, cudaStream_t st, int64_t* launches);
+void square_values(const double* s, double* out, int k, cudaStream_t st, int64_t* launches);
+
+}  // namespace fig

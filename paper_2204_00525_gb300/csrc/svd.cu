@@ -1,0 +1,134 @@
+// SVD of R (§8.2): sigma(A) = sigma(R) and V(A) = V(R); PCA (§8.3) takes the leading
+// columns of V.  R is N x N, so a one-sided (Hestenes) Jacobi SVD in FP64 in one
+// thread block suffices: columns of W = R are rotated pairwise until orthogonal;
+// sigma_j = ||W_j|| and V accumulates the rotations.  The paper used LAPACK's
+// divide and conquer on the CPU; one-sided Jacobi is chosen here for its high relative
+// accuracy and because every pair of a round-robin round can be rotated in parallel.
+#include "kernels.cuh"
+
+namespace fig {
+
+constexpr int kSvdThreads = 256;
+constexpr int kSvdMaxSweeps = 40;
+
+__global__ void __launch_bounds__(kSvdThreads) k_jacobi(const double* R, int64_t ldr, int N, double* Wg,
+                                                        double* Vg, double* sigma, double* Vout, int use_smem,
+                                                        int* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int rotations;
+  double* W = use_smem ? reinterpret_cast<double*>(smem_raw) : Wg;   // column j at W + j N
+  double* V = use_smem ? W + (int64_t)N * N : Vg;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int idx = tid; idx < N * N; idx += blockDim.x) {
+    const int j = idx / N, i = idx - j * N;
+    W[idx] = R[(int64_t)i * ldr + j];
+    V[idx] = i == j ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int npad = N + (N & 1);
+  int sweep = 0;
+  for (; sweep < kSvdMaxSweeps; ++sweep) {
+    if (tid == 0) rotations = 0;
+    __syncthreads();
+    for (int r = 0; r < npad - 1; ++r) {
+      // round-robin (circle) schedule: position 0 holds player 0, position k >= 1
+      // holds player 1 + (k - 1 + r) mod (npad - 1); pair positions i and npad-1-i.
+      for (int pi = warp; pi < npad / 2; pi += nw) {
+        const int pa = pi, pb = npad - 1 - pi;
+        const int a = pa == 0 ? 0 : 1 + (pa - 1 + r) % (npad - 1);
+        const int b = 1 + (pb - 1 + r) % (npad - 1);
+        if (a >= N || b >= N) continue;
+        const int p = a < b ? a : b, q = a < b ? b : a;
+        double* wp = W + (int64_t)p * N;
+        double* wq = W + (int64_t)q * N;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int i = lane; i < N; i += 32) {
+          const double x = wp[i], y = wq[i];
+          al = fma(x, x, al);
+          be = fma(y, y, be);
+          ga = fma(x, y, ga);
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (fabs(ga) > 1e-15 * sqrt(al * be) && fabs(ga) > 1e-300) {
+          const double zeta = (be - al) / (2.0 * ga);
+          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+          double* vp = V + (int64_t)p * N;
+          double* vq = V + (int64_t)q * N;
+          for (int i = lane; i < N; i += 32) {
+            const double x = wp[i], y = wq[i];
+            wp[i] = c * x - s * y;
+            wq[i] = s * x + c * y;
+            const double u = vp[i], w = vq[i];
+            vp[i] = c * u - s * w;
+            vq[i] = s * u + c * w;
+          }
+          if (lane == 0) atomicAdd(&rotations, 1);
+        }
+      }
+      __syncthreads();
+    }
+    const int rot = rotations;
+    __syncthreads();
+    if (rot == 0) break;
+  }
+  if (sweep == kSvdMaxSweeps && tid == 0) set_error(err, FIGARO_ERR_TIMEOUT);
+  // sigma_j = ||W_j||, kept in the first row of the scratch after the loop
+  double* sig = reinterpret_cast<double*>(smem_raw) + (use_smem ? 2 * (int64_t)N * N : 0);
+  for (int j = warp; j < N; j += nw) {
+    double s2 = 0.0;
+    for (int i = lane; i < N; i += 32) s2 = fma(W[(int64_t)j * N + i], W[(int64_t)j * N + i], s2);
+    s2 = warp_sum(s2);
+    if (lane == 0) sig[j] = sqrt(s2);
+  }
+  __syncthreads();
+  // descending order, ties by index; every column signed so its largest entry is positive
+  for (int j = warp; j < N; j += nw) {
+    const double sj = sig[j];
+    int rank = 0;
+    for (int k = lane; k < N; k += 32) rank += (sig[k] > sj || (sig[k] == sj && k < j)) ? 1 : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o);
+    const double* vj = V + (int64_t)j * N;
+    double best = -1.0;
+    int arg = 0;
+    for (int i = lane; i < N; i += 32) {
+      const double a = fabs(vj[i]);
+      if (a > best) { best = a; arg = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oa = __shfl_xor_sync(0xffffffffu, arg, o);
+      if (ob > best || (ob == best && oa < arg)) { best = ob; arg = oa; }
+    }
+    const double sgn = vj[arg] < 0.0 ? -1.0 : 1.0;
+    if (lane == 0) sigma[rank] = sj;
+    for (int i = lane; i < N; i += 32) Vout[(int64_t)i * N + rank] = sgn * vj[i];
+  }
+}
+
+__global__ void k_square(const double* s, double* out, int k) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) out[i] = s[i] * s[i];
+}
+
+size_t jacobi_smem(int N) { return (2 * (size_t)N * N + N) * sizeof(double); }
+
+void jacobi_svd(const double* R, int64_t ldr, int N, double* W, double* V, double* sigma, double* Vout,
+                int* err, cudaStream_t st, int64_t* launches) {
+  size_t smem = jacobi_smem(N);
+  const int use_smem = smem <= 200 * 1024;
+  if (!use_smem) smem = (size_t)N * sizeof(double);
+  cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_jacobi<<<1, kSvdThreads, smem, st>>>(R, ldr, N, W, V, sigma, Vout, use_smem, err);
+  ++*launches;
+}
+
+void square_values(const double* s, double* out, int k, cudaStream_t st, int64_t* launches) {
+  k_square<<<1, 256, 0, st>>>(s, out, k);
+  ++*launches;
+}
+
+}  // namespace fig
