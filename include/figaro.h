@@ -201,6 +201,26 @@ enum {
 };
 int64_t figaro_debug_read(figaro_plan_t plan, int32_t rel, int32_t what, void* dst, int64_t bytes);
 
+/* SVD of a given N x N matrix R (row-major, leading dimension ldr >= N, device memory)
+ * without any device allocation: the paper has no counterpart; this entry point exists for
+ * callers that cannot allocate device memory when they need the SVD -- for example a
+ * process whose device memory is entirely reserved by its own pool allocator, or a
+ * latency-critical loop in which the implicit synchronisation of an allocation is not
+ * acceptable.  The caller passes R and the outputs: sigma[N] (descending) and V (N x N
+ * row-major, column j the j-th right singular vector, signed so that its largest-magnitude
+ * entry is positive), both device pointers, exactly as figaro_svd returns them.
+ * Work arrays live in one fixed device array of 2 * 256 * 256 doubles plus an error word
+ * (about 1 MiB), defined in the library and held by every GPU that loads it until the
+ * process exits; N larger than 256 is rejected with FIGARO_ERR_UNSUPPORTED before any
+ * device work.  The first call on a device looks up that array's device address (once per
+ * device, with the device current); make that first call before any stream capture.  All
+ * calls share the array: calls whose executions overlap on the GPU (other streams, other
+ * host threads) race and must be serialised by the caller.  Enqueues on `stream` and
+ * waits for it before returning.  Errors: INVALID_ARG, UNSUPPORTED, TIMEOUT (no
+ * convergence in 40 sweeps), CUDA. */
+int figaro_svd_from_r_static(const double* R, int64_t ldr, int32_t n, double* sigma, double* V,
+                             void* stream);
+
 /* Name of a status code (static storage). */
 const char* figaro_error_string(int status);
 

@@ -79,6 +79,7 @@ def load(build_if_missing: bool = False):
         "figaro_stage_times": (C.c_int, [P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),
         "figaro_reset_stage_times": (C.c_int, [P]),
         "figaro_debug_read": (C.c_int64, [P, C.c_int32, C.c_int32, P, C.c_int64]),
+        "figaro_svd_from_r_static": (C.c_int, [P, C.c_int64, C.c_int32, P, P, P]),
         "figaro_error_string": (C.c_char_p, [C.c_int]),
         "figaro_last_error": (C.c_char_p, []),
     }
@@ -122,6 +123,11 @@ def figaro_svd(plan, sigma_ptr: int, V_ptr: int, R_ptr: int = 0):
 
 def figaro_pca(plan, k: int, comp_ptr: int, eig_ptr: int):
     return check(load().figaro_pca(plan, k, C.c_void_p(comp_ptr), C.c_void_p(eig_ptr)))
+
+
+def figaro_svd_from_r_static(R_ptr: int, ldr: int, n: int, sigma_ptr: int, V_ptr: int, stream: int):
+    return check(load().figaro_svd_from_r_static(C.c_void_p(R_ptr), ldr, n, C.c_void_p(sigma_ptr),
+                                                 C.c_void_p(V_ptr), C.c_void_p(stream)))
 
 
 def figaro_plan_destroy(plan):

@@ -132,3 +132,68 @@ void square_values(const double* s, double* out, int k, cudaStream_t st, int64_t
 }
 
 }  // namespace fig
+
+// ------------------------------------------------------------------ allocation-free variant
+// figaro_svd_from_r_static: the same Jacobi kernel, with its W and V work arrays in one
+// fixed device array owned by this library instead of memory the caller or a plan
+// allocates.  Some callers cannot allocate device memory at the moment they need an SVD
+// (a process whose device memory is fully reserved by its own pool, a latency-critical
+// loop where an allocation's implicit synchronisation is not allowed); they still pass
+// R, sigma and V themselves.
+#include <mutex>
+
+namespace fig {
+
+constexpr int kStaticSvdMaxN = 256;
+// W (N x N) + V (N x N) for N <= 256, followed by one error word: 1 MiB + 256 bytes,
+// held on every device that loads this library until the process exits.
+static __device__ __align__(256) double g_svd_static_scratch[2 * kStaticSvdMaxN * kStaticSvdMaxN + 32];
+
+constexpr int kStaticMaxDevices = 64;
+static double* g_svd_static_ptr[kStaticMaxDevices] = {nullptr};
+static std::mutex g_svd_static_mutex;
+
+// Device address of the static array on the current device, looked up once per device
+// (host code only holds a host-side stand-in for the symbol, which must not be passed to
+// a kernel).
+static int static_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return FIGARO_ERR_CUDA;
+  if (dev < 0 || dev >= kStaticMaxDevices) return FIGARO_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_svd_static_mutex);
+  if (!g_svd_static_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_svd_static_scratch);
+    if (e != cudaSuccess || !p) return FIGARO_ERR_CUDA;
+    g_svd_static_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_svd_static_ptr[dev];
+  return FIGARO_OK;
+}
+
+}  // namespace fig
+
+extern "C" int figaro_svd_from_r_static(const double* R, int64_t ldr, int32_t n, double* sigma, double* V,
+                                        void* stream) {
+  using namespace fig;
+  if (!R || !sigma || !V || n < 1 || ldr < n) return FIGARO_ERR_INVALID_ARG;
+  if (n > kStaticSvdMaxN) return FIGARO_ERR_UNSUPPORTED;
+  double* base = nullptr;
+  int rc = static_scratch(&base);
+  if (rc != FIGARO_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double* W = base;
+  double* Vw = base + (int64_t)n * n;
+  int* err = reinterpret_cast<int*>(base + 2 * kStaticSvdMaxN * kStaticSvdMaxN);
+  // the error word keeps the previous call's value: clear it first
+  if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return FIGARO_ERR_CUDA;
+  const size_t smem = (size_t)n * sizeof(double);
+  k_jacobi<<<1, kSvdThreads, smem, st>>>(R, ldr, n, W, Vw, sigma, V, 0, err);
+  int host_err = 0;
+  if (cudaGetLastError() != cudaSuccess) return FIGARO_ERR_CUDA;
+  if (cudaMemcpyAsync(&host_err, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return FIGARO_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return FIGARO_ERR_CUDA;
+  return host_err;
+}
