@@ -82,9 +82,13 @@ struct figaro_plan_s {
   int32_t* radix_scan_tmp = nullptr;
   std::vector<fig::TsqrBlock> blocks;
   fig::TsqrBlock* blocks_dev = nullptr;
-  void* tsqr_scratch = nullptr;
   int stack_rows = 0;
   double* stack = nullptr;
+  fig::TsqrBlock stack_blk{};          // the stacked block triangles (final QR)
+  std::vector<cudaStream_t> side;      // one stream per R0 block: the TSQR chains run concurrently
+  std::vector<cudaEvent_t> side_done;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> leaf_ev;    // stage timing: start/end of every block's leaf kernel
   double* Rtmp = nullptr;
   double* svdW = nullptr;
   double* svdV = nullptr;
@@ -182,16 +186,22 @@ static void layout(figaro_plan_s& P, Arena& a) {
     b.tcarry = a.take<double>(n.n_tiles * wide);
     b.coldesc = a.take<int2>(std::max(n.N_sub, 1));
   }
-  int64_t scratch = 0;
   for (auto& blk : P.blocks) {
     blk.tri[0] = a.take<double>(tsqr_tri_elems(blk));
     blk.tri[1] = a.take<double>(tsqr_tri_elems(blk));
     blk.cols = a.take<int>(blk.n);
-    scratch = std::max(scratch, tsqr_scratch_elems(blk, mixed));
+    const int64_t sc = tsqr_scratch_elems(blk, mixed);
+    blk.scratch = sc ? a.take<double>(sc) : nullptr;
   }
-  P.tsqr_scratch = a.take<double>(scratch);
+  {
+    const int64_t sc = tsqr_scratch_elems(P.stack_blk, false);
+    P.stack_blk.scratch = sc ? a.take<double>(sc) : nullptr;
+  }
   P.blocks_dev = a.take<TsqrBlock>((int64_t)P.blocks.size());
   P.stack = a.take<double>((int64_t)P.stack_rows * P.N);
+  P.stack_blk.ptr = P.stack;
+  P.stack_blk.tri[0] = a.take<double>(tsqr_tri_elems(P.stack_blk));
+  P.stack_blk.tri[1] = a.take<double>(tsqr_tri_elems(P.stack_blk));
   const int64_t NN = (int64_t)P.N * P.N;
   P.Rtmp = a.take<double>(NN);
   P.svdW = a.take<double>(NN);
@@ -473,6 +483,14 @@ static void make_blocks(figaro_plan_s& P) {
       P.stack_rows += t.n;
     }
   }
+  TsqrBlock s{};
+  s.n = P.N;
+  s.kind = BLK_FIXED;
+  s.M = P.stack_rows;
+  s.bound = P.stack_rows;
+  s.ld = P.stack_rows;
+  tsqr_plan_block(s, false);
+  P.stack_blk = s;
 }
 
 // block pointers that depend on the arena
@@ -691,14 +709,25 @@ static int run_r(figaro_plan_s& P, double* R, int64_t ldr) {
     if (gp.N > 0) gen_heads_tails(gp, st, &P.launches);
   }
   clk.stop();
-  // ---- stage 5: TSQR leaves
-  clk.start(5);
-  for (auto& b : P.blocks) tsqr_leaf(b, mixed, P.tsqr_scratch, st, &P.launches);
-  clk.stop();
-  // ---- stage 6: TSQR tree + final
+  // ---- stages 5-6: TSQR of every R0 block, each on its own stream (the blocks are
+  // independent), then the final QR of their stacked triangles on the main stream.
+  // Stage 5 sums the leaf kernels' durations (timed on their own streams, so they may
+  // overlap); stage 6 is the wall time of the whole TSQR section.
   clk.start(6);
-  for (auto& b : P.blocks) tsqr_reduce(b, P.tsqr_scratch, st, &P.launches);
-  tsqr_final(P.blocks_dev, (int)P.blocks.size(), P.stack_rows, P.N, P.stack, R, ldr, st, &P.launches);
+  FIG_CUDA(cudaEventRecord(P.fork, st));
+  for (size_t bi = 0; bi < P.blocks.size(); ++bi) {
+    cudaStream_t s = P.side[bi];
+    FIG_CUDA(cudaStreamWaitEvent(s, P.fork, 0));
+    if (P.opt.stage_timing) FIG_CUDA(cudaEventRecord(P.leaf_ev[2 * bi], s));
+    const int64_t l0 = P.launches;
+    tsqr_leaf(P.blocks[bi], mixed, s, &P.launches);
+    P.stage_launch[5] += P.launches - l0;
+    if (P.opt.stage_timing) FIG_CUDA(cudaEventRecord(P.leaf_ev[2 * bi + 1], s));
+    tsqr_reduce(P.blocks[bi], s, &P.launches);
+    FIG_CUDA(cudaEventRecord(P.side_done[bi], s));
+    FIG_CUDA(cudaStreamWaitEvent(st, P.side_done[bi], 0));
+  }
+  tsqr_final(P.blocks_dev, (int)P.blocks.size(), P.stack_blk, R, ldr, st, &P.launches);
   clk.stop();
   FIG_CUDA(cudaGetLastError());
   return FIGARO_OK;
@@ -713,8 +742,14 @@ static int finish(figaro_plan_s& P, int stages_used) {
   FIG_CUDA(cudaGetLastError());
   if (P.opt.stage_timing) {
     for (int s = 0; s < stages_used; ++s) {
+      if (s == 5) continue;                      // stage 5 is measured per block below
       float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, P.ev[s], P.ev[s + 1]) == cudaSuccess) P.stage_ms[s] += ms;
+      const int from = s == 6 ? 6 : s;           // stage 6 starts at its own event
+      if (cudaEventElapsedTime(&ms, P.ev[from], P.ev[s + 1]) == cudaSuccess) P.stage_ms[s] += ms;
+    }
+    for (size_t bi = 0; bi < P.blocks.size(); ++bi) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, P.leaf_ev[2 * bi], P.leaf_ev[2 * bi + 1]) == cudaSuccess) P.stage_ms[5] += ms;
     }
   }
   // bookkeeping for figaro_plan_get_info: R0 rows and TSQR leaf flops of this call
@@ -769,6 +804,13 @@ int figaro_plan_destroy(figaro_plan_t p) {
   if (p->arena) cudaStreamSynchronize(p->st);
   for (auto& e : p->ev)
     if (e) cudaEventDestroy(e);
+  for (auto& e : p->side_done)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : p->leaf_ev)
+    if (e) cudaEventDestroy(e);
+  if (p->fork) cudaEventDestroy(p->fork);
+  for (auto& s : p->side)
+    if (s) cudaStreamDestroy(s);
   if (p->err_host) cudaFreeHost(p->err_host);
   if (p->arena) cudaFree(p->arena);
   delete p;
@@ -821,6 +863,20 @@ int figaro_plan(const figaro_join_tree* tree, const figaro_options* opt, void* s
   cudaError_t e = cudaMallocHost(&P->err_host, sizeof(int) * (4 + 4 * P->nodes.size()));
   if (e != cudaSuccess) return bail(e, "cudaMallocHost");
   for (auto& ev : P->ev) {
+    e = cudaEventCreate(&ev);
+    if (e != cudaSuccess) return bail(e, "cudaEventCreate");
+  }
+  e = cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming);
+  if (e != cudaSuccess) return bail(e, "cudaEventCreate");
+  P->side.assign(P->blocks.size(), nullptr);
+  P->side_done.assign(P->blocks.size(), nullptr);
+  for (size_t bi = 0; bi < P->blocks.size(); ++bi) {
+    e = cudaStreamCreateWithFlags(&P->side[bi], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->side_done[bi], cudaEventDisableTiming);
+    if (e != cudaSuccess) return bail(e, "side streams");
+  }
+  P->leaf_ev.assign(2 * P->blocks.size(), nullptr);
+  for (auto& ev : P->leaf_ev) {
     e = cudaEventCreate(&ev);
     if (e != cudaSuccess) return bail(e, "cudaEventCreate");
   }

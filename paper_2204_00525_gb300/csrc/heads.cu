@@ -5,8 +5,8 @@
 // hold a sixth of a relation, so here the sorted rows are cut into fixed tiles of
 // 256 elements per warp regardless of group boundaries.  Per column, a prefix sum that
 // restarts at every group start is computed in three steps: (1) every tile reports
-// whether it contains a group start and the sum after its last start, (2) one warp per
-// column scans those tile aggregates into a carry per tile, (3) every tile recomputes its
+// whether it contains a group start and the sum after its last start, (2) one thread
+// block per column scans those tile aggregates into a carry per tile, (3) every tile recomputes its
 // prefix sums with the carry and writes tail rows and heads.
 //
 // Tail of a group with rows a_0..a_{m-1} (0-based position p, exclusive prefix S_p):
@@ -52,28 +52,54 @@ void beta_table(double* beta, int64_t len, cudaStream_t st) {
   k_beta<<<grid_for(len, 256, 4096), 256, 0, st>>>(beta, len);
 }
 
-// One warp per column: carry[c][t] = sum of the column since the last group start before
-// tile t (0 if tile t begins a group).
-__global__ void k_tile_carry(const uint8_t* tflag, const double* tsum, double* tcarry, int64_t nt, int N) {
-  const int lane = threadIdx.x & 31;
-  const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (c >= N) return;
-  const uint8_t* f_in = tflag + (int64_t)c * nt;
-  const double* s_in = tsum + (int64_t)c * nt;
-  double* out = tcarry + (int64_t)c * nt;
-  double run = 0.0;
-  for (int64_t base = 0; base < nt; base += 32) {
-    const int64_t t = base + lane;
-    int fi = t < nt ? (int)f_in[t] : 0;
-    double si = t < nt ? s_in[t] : 0.0;
-    pair_scan_incl(fi, si, lane);
-    int fe = __shfl_up_sync(0xffffffffu, fi, 1);
-    double se = __shfl_up_sync(0xffffffffu, si, 1);
-    if (lane == 0) { fe = 0; se = 0.0; }
-    if (t < nt) out[t] = fe ? se : run + se;
-    const int f31 = __shfl_sync(0xffffffffu, fi, 31);
-    const double s31 = __shfl_sync(0xffffffffu, si, 31);
-    run = f31 ? s31 : run + s31;
+// One block of 1024 threads per column: carry[c][t] = sum of the column since the last
+// group start before tile t (0 if tile t begins a group).  Each thread reduces a
+// contiguous run of tiles, a block-wide scan of (flag, sum) pairs gives every run its
+// incoming carry, and the run is then walked again to write the carries.  `live` (if
+// set) holds the element count whose tiles are live.
+constexpr int kCarryThreads = 1024;
+
+__global__ void __launch_bounds__(kCarryThreads) k_tile_carry(const uint8_t* tflag, const double* tsum,
+                                                              double* tcarry, int64_t nt_alloc,
+                                                              const int32_t* live) {
+  __shared__ int wf[32];
+  __shared__ double ws[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t nt = live ? ((int64_t)live[0] + kHtTile - 1) / kHtTile : nt_alloc;
+  const uint8_t* f_in = tflag + (int64_t)blockIdx.x * nt_alloc;
+  const double* s_in = tsum + (int64_t)blockIdx.x * nt_alloc;
+  double* out = tcarry + (int64_t)blockIdx.x * nt_alloc;
+  const int64_t chunk = (nt + kCarryThreads - 1) / kCarryThreads;
+  const int64_t t0 = (int64_t)threadIdx.x * chunk;
+  const int64_t t1 = t0 + chunk < nt ? t0 + chunk : nt;
+  int f = 0;
+  double s = 0.0;
+  for (int64_t t = t0; t < t1; ++t) {
+    if (f_in[t]) { f = 1; s = s_in[t]; } else { s += s_in[t]; }
+  }
+  int fi = f;
+  double si = s;
+  pair_scan_incl(fi, si, lane);
+  int fe = __shfl_up_sync(0xffffffffu, fi, 1);
+  double se = __shfl_up_sync(0xffffffffu, si, 1);
+  if (lane == 0) { fe = 0; se = 0.0; }
+  if (lane == 31) { wf[warp] = fi; ws[warp] = si; }
+  __syncthreads();
+  if (warp == 0) {
+    int a = wf[lane];
+    double b = ws[lane];
+    pair_scan_incl(a, b, lane);
+    int ae = __shfl_up_sync(0xffffffffu, a, 1);
+    double be = __shfl_up_sync(0xffffffffu, b, 1);
+    if (lane == 0) { ae = 0; be = 0.0; }
+    wf[lane] = ae;
+    ws[lane] = be;
+  }
+  __syncthreads();
+  double run = fe ? se : ws[warp] + se;
+  for (int64_t t = t0; t < t1; ++t) {
+    out[t] = run;
+    run = f_in[t] ? s_in[t] : run + s_in[t];
   }
 }
 
@@ -183,7 +209,7 @@ void leaf_heads_tails(const LeafParams& p, cudaStream_t st, int64_t* launches) {
   if (p.N == 0) return;
   const unsigned g = ht_grid(p.n_tiles);
   k_leaf_agg<<<g, 256, 0, st>>>(p);
-  k_tile_carry<<<(p.N + 7) / 8, 256, 0, st>>>(p.tflag, p.tsum, p.tcarry, p.n_tiles, p.N);
+  k_tile_carry<<<p.N, kCarryThreads, 0, st>>>(p.tflag, p.tsum, p.tcarry, p.n_tiles, nullptr);
   k_leaf_emit<<<g, 256, 0, st>>>(p);
   *launches += 3;
 }
@@ -321,7 +347,7 @@ void gen_heads_tails(const GenParams& p, cudaStream_t st, int64_t* launches) {
   }
   const unsigned g = ht_grid(p.n_tiles);
   k_gen_agg<<<g, 256, 0, st>>>(p);
-  k_tile_carry<<<(p.N + 7) / 8, 256, 0, st>>>(p.tflag, p.tsum, p.tcarry, p.n_tiles, p.N);
+  k_tile_carry<<<p.N, kCarryThreads, 0, st>>>(p.tflag, p.tsum, p.tcarry, p.n_tiles, p.sizes);
   k_gen_emit<<<g, 256, 0, st>>>(p);
   *launches += 3;
 }

@@ -172,7 +172,7 @@ void leaf_heads_tails(const LeafParams& p, cudaStream_t st, int64_t* launches);
 void gen_heads_tails(const GenParams& p, cudaStream_t st, int64_t* launches);
 
 // ------------------------------------------------------------------ tsqr.cu
-enum BlockKind : int { BLK_TAILS = 0, BLK_GEN = 1, BLK_ROOT = 2 };
+enum BlockKind : int { BLK_TAILS = 0, BLK_GEN = 1, BLK_ROOT = 2, BLK_FIXED = 3 };
 
 struct TsqrBlock {
   const double* ptr;         // col-major, leading dimension ld
@@ -180,23 +180,27 @@ struct TsqrBlock {
   int n;                     // columns
   int kind;
   int64_t M;
-  const int32_t* sizes;      // rows = M - G (tails), G - P (gen), G (root)
+  const int32_t* sizes;      // rows = M - G (tails), G - P (gen), G (root), M (fixed)
   int64_t bound;             // allocation bound of rows
   int tile;                  // leaf tile rows
   int fan;                   // triangles merged per reduce tile
   int levels;                // reduce levels after the leaf
   double* tri[2];            // ping-pong triangle buffers [bound tiles x n x n]
   int top;                   // buffer holding the last level
+  int nreg;                  // register path: columns padded to an even count <= 16; 0 = not used
+  int nw;                    // shared-memory warp path: columns padded to 8, 16 or 32; 0 = not used
+  int wpc;                   // warp path: warps (tiles) per thread block
   const int* cols;           // device [n]: global column of each block column
+  void* scratch;             // block path: global tile slots when a tile exceeds shared memory
 };
 
 void tsqr_plan_block(TsqrBlock& b, bool mixed);
 int64_t tsqr_tri_elems(const TsqrBlock& b);
 int64_t tsqr_scratch_elems(const TsqrBlock& b, bool mixed);
-void tsqr_leaf(const TsqrBlock& b, bool mixed, void* scratch, cudaStream_t st, int64_t* launches);
-void tsqr_reduce(TsqrBlock& b, void* scratch, cudaStream_t st, int64_t* launches);
-void tsqr_final(const TsqrBlock* blocks_dev, int n_blocks, int stack_rows, int N, double* stack,
-                double* R, int64_t ldr, cudaStream_t st, int64_t* launches);
+void tsqr_leaf(const TsqrBlock& b, bool mixed, cudaStream_t st, int64_t* launches);
+void tsqr_reduce(TsqrBlock& b, cudaStream_t st, int64_t* launches);
+void tsqr_final(const TsqrBlock* blocks_dev, int n_blocks, TsqrBlock& stack_blk, double* R, int64_t ldr,
+                cudaStream_t st, int64_t* launches);
 double tsqr_leaf_flops(int64_t rows, int n);
 
 // ------------------------------------------------------------------ svd.cu

@@ -4,31 +4,29 @@
 // of a node, the root Data) on its own columns and then the stack of the resulting
 // triangles.  Each block is cut into row tiles; every tile is reduced by Householder
 // QR to an n x n triangle (leaf), groups of `fan` triangles are stacked and reduced
-// again until one triangle per block remains (tree), and the block triangles, placed
-// at their global columns, are reduced by a final QR to R.  The paper's own choices
-// were Householder (MKL) or per-thread Givens (THIN); the TSQR tree is the GPU form of
-// the same block-then-stack scheme.
+// again until one triangle per block remains (tree).  The block triangles, placed at
+// their global columns, form one more block (the stack) that goes through the same leaf
+// and tree kernels; its triangle, sign-normalised, is R.  The paper's own choices were
+// Householder (MKL) or per-thread Givens (THIN); the TSQR tree is the GPU form of the
+// same block-then-stack scheme.
+//
+// Two kernels do the QR of a tile:
+//   n <= 32: one warp per tile, the tile in registers (k_tsqr_reg), every loop bound a
+//            compile-time constant so that no predicated-off FP64 instruction is issued;
+//   n >  32: one thread block per tile in shared memory (k_tsqr_cta).
+// Both are persistent over the live tiles: the row counts are only known on the device.
 //
 // Precision: FP64 throughout, or (mixed) FP32 leaf tiles with FP64 tree and final QR.
-#include "kernels.cuh"
+#include "tsqr_reg.cuh"
 
 namespace fig {
 
 constexpr int kQrThreads = 256;
 constexpr size_t kSmemCap = 200 * 1024;
 
-__device__ __forceinline__ int64_t block_rows(const TsqrBlock& b) {
-  const int32_t G = b.sizes[0], P = b.sizes[1];
-  switch (b.kind) {
-    case BLK_TAILS: return b.M - G;
-    case BLK_GEN: return (int64_t)G - P;
-    default: return G;
-  }
-}
-
+// ------------------------------------------------------------------ block path (n > 32)
 // Householder QR of the m x n column-major matrix A (leading dimension lda) by the
-// whole block.  On return the upper triangle of A[0:min(m,n), :] holds R (diagonal of
-// either sign); the reflector of column k is x -> beta e_1 with beta = -sign(x_0)||x||.
+// whole thread block.  On return the upper triangle of A[0:min(m,n), :] holds R.
 template <typename E>
 __device__ void hh_qr(E* A, int lda, int m, int n, E* red) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -39,12 +37,12 @@ __device__ void hh_qr(E* A, int lda, int m, int n, E* red) {
     for (int i = k + 1 + tid; i < m; i += blockDim.x) s = fma(ak[i], ak[i], s);
     s = block_sum<E>(s, red);
     const E alpha = ak[k];
-    if (s == E(0)) continue;                         // column already reduced below k
+    if (s == E(0)) continue;
     const E normx = sqrt(fma(alpha, alpha, s));
     const E beta = alpha >= E(0) ? -normx : normx;
     const E tau = (beta - alpha) / beta;
     const E scal = E(1) / (alpha - beta);
-    __syncthreads();                                  // alpha read by everyone
+    __syncthreads();
     for (int i = k + 1 + tid; i < m; i += blockDim.x) ak[i] *= scal;   // v, with v_k = 1
     if (tid == 0) ak[k] = beta;
     __syncthreads();
@@ -63,66 +61,57 @@ __device__ void hh_qr(E* A, int lda, int m, int n, E* red) {
   }
 }
 
-// Leaf: tile blockIdx.x of the block's rows -> n x n triangle (zeros below the diagonal).
+// One thread block per tile (persistent).  The tile sits in shared memory, or in a
+// global scratch slot per block when it does not fit.
+// With few_only set (tree levels that the warp-per-tile kernel also serves) it works only
+// on levels with fewer than kWarpModeTiles tiles.
 template <typename E>
-__global__ void __launch_bounds__(kQrThreads) k_tsqr_leaf(TsqrBlock b, E* gscratch) {
+__global__ void __launch_bounds__(kQrThreads) k_tsqr_cta(TsqrBlock b, const double* tri_in, double* tri_out,
+                                                         int64_t div_in, E* gscratch, int few_only) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int64_t rows = block_rows(b);
-  const int64_t r0 = (int64_t)blockIdx.x * b.tile;
-  if (r0 >= rows) return;
-  const int n = b.n, T = b.tile;
-  const int m = (int)((rows - r0) < T ? (rows - r0) : T);
+  if (copy_single(b, rows, div_in, tri_in, tri_out)) return;
+  if (few_only && level_tiles(b, rows, div_in, false) >= kWarpModeTiles) return;
+  const int n = b.n;
+  const int lda = tri_in ? b.fan * n : b.tile;
   E* red = reinterpret_cast<E*>(smem_raw);
-  E* A = gscratch ? gscratch + (int64_t)blockIdx.x * T * n : red + 64;
-  for (int c = 0; c < n; ++c)
-    for (int i = threadIdx.x; i < m; i += blockDim.x)
-      A[(int64_t)c * T + i] = (E)b.ptr[(int64_t)c * b.ld + r0 + i];
-  __syncthreads();
-  hh_qr<E>(A, T, m, n, red);
-  double* tri = b.tri[0] + (int64_t)blockIdx.x * n * n;
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    const int c = idx / n, r = idx - c * n;
-    tri[idx] = (r <= c && r < m) ? (double)A[(int64_t)c * T + r] : 0.0;
+  E* A = gscratch ? gscratch + (int64_t)blockIdx.x * lda * n : red + 64;
+  const int64_t nt_in = tri_in ? (rows + div_in - 1) / div_in : 0;
+  const int64_t n_tiles = level_tiles(b, rows, div_in, tri_in == nullptr);
+  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    int m;
+    if (!tri_in) {
+      const int64_t r0 = t * b.tile;
+      m = (int)((rows - r0) < b.tile ? (rows - r0) : b.tile);
+      for (int c = 0; c < n; ++c)
+        for (int i = threadIdx.x; i < m; i += blockDim.x)
+          A[(int64_t)c * lda + i] = (E)b.ptr[(int64_t)c * b.ld + r0 + i];
+    } else {
+      const int64_t first = t * b.fan;
+      const int cnt = (int)((nt_in - first) < b.fan ? (nt_in - first) : b.fan);
+      m = cnt * n;
+      for (int idx = threadIdx.x; idx < m * n; idx += blockDim.x) {
+        const int c = idx / m, rr = idx - c * m;
+        const int f = rr / n, r = rr - f * n;
+        A[(int64_t)c * lda + rr] = (E)tri_in[(first + f) * n * n + (int64_t)c * n + r];
+      }
+    }
+    __syncthreads();
+    hh_qr<E>(A, lda, m, n, red);
+    double* tri = tri_out + t * n * n;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      const int c = idx / n, r = idx - c * n;
+      tri[idx] = (r <= c && r < m) ? (double)A[(int64_t)c * lda + r] : 0.0;
+    }
+    __syncthreads();
   }
 }
 
-// Tree level: stack `fan` triangles of the previous level and reduce them to one.
-__global__ void __launch_bounds__(kQrThreads) k_tsqr_reduce(TsqrBlock b, const double* tri_in, double* tri_out,
-                                                           int64_t div_in, double* gscratch) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int64_t rows = block_rows(b);
-  const int64_t nt_in = (rows + div_in - 1) / div_in;
-  const int64_t first = (int64_t)blockIdx.x * b.fan;
-  if (first >= nt_in) return;
-  const int n = b.n, F = b.fan;
-  const int cnt = (int)((nt_in - first) < F ? (nt_in - first) : F);
-  const int lda = F * n, m = cnt * n;
-  double* red = reinterpret_cast<double*>(smem_raw);
-  double* A = gscratch ? gscratch + (int64_t)blockIdx.x * lda * n : red + 64;
-  for (int idx = threadIdx.x; idx < m * n; idx += blockDim.x) {
-    const int c = idx / m, rr = idx - c * m;
-    const int f = rr / n, r = rr - f * n;
-    A[(int64_t)c * lda + rr] = tri_in[(first + f) * n * n + (int64_t)c * n + r];
-  }
-  __syncthreads();
-  hh_qr<double>(A, lda, m, n, red);
-  double* tri = tri_out + (int64_t)blockIdx.x * n * n;
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    const int c = idx / n, r = idx - c * n;
-    tri[idx] = (r <= c && r < m) ? A[(int64_t)c * lda + r] : 0.0;
-  }
-}
-
-// Final: place every block's triangle at its global columns, QR the stack, write R
-// row-major with a non-negative diagonal and zeros below it.
-__global__ void __launch_bounds__(kQrThreads) k_tsqr_final(const TsqrBlock* blocks, int nb, int stack_rows,
-                                                          int N, double* stack, double* R, int64_t ldr,
-                                                          int use_smem) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* red = reinterpret_cast<double*>(smem_raw);
-  double* A = use_smem ? red + 64 : stack;
-  const int lda = stack_rows;
-  for (int idx = threadIdx.x; idx < stack_rows * N; idx += blockDim.x) A[idx] = 0.0;
+// ------------------------------------------------------------------ final stack and R
+// One thread block places every block's triangle at its global columns: stack rows
+// [off_b, off_b + n_b), column-major with leading dimension stack_rows.
+__global__ void k_tsqr_stack(const TsqrBlock* blocks, int nb, int stack_rows, int N, double* stack) {
+  for (int idx = threadIdx.x; idx < stack_rows * N; idx += blockDim.x) stack[idx] = 0.0;
   __syncthreads();
   int off = 0;
   for (int bi = 0; bi < nb; ++bi) {
@@ -132,42 +121,68 @@ __global__ void __launch_bounds__(kQrThreads) k_tsqr_final(const TsqrBlock* bloc
       const double* tri = b.tri[b.top];
       for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
         const int c = idx / n, r = idx - c * n;
-        A[(int64_t)b.cols[c] * lda + off + r] = tri[idx];
+        stack[(int64_t)b.cols[c] * stack_rows + off + r] = tri[idx];
       }
     }
     off += n;
   }
-  __syncthreads();
-  hh_qr<double>(A, lda, stack_rows, N, red);
-  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+}
+
+// R = the stack's triangle with every row multiplied by the sign of its diagonal entry.
+__global__ void k_write_r(const double* tri, int N, double* R, int64_t ldr) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N * N; idx += gridDim.x * blockDim.x) {
     const int i = idx / N, j = idx - i * N;
     double v = 0.0;
-    if (j >= i && i < stack_rows) {
-      const double d = A[(int64_t)i * lda + i];
-      v = (d < 0.0 ? -1.0 : 1.0) * A[(int64_t)j * lda + i];
+    if (j >= i) {
+      const double d = tri[(int64_t)i * N + i];
+      v = (d < 0.0 ? -1.0 : 1.0) * tri[(int64_t)j * N + i];
     }
     R[(int64_t)i * ldr + j] = v;
   }
 }
 
 // ------------------------------------------------------------------ host planning
-static size_t leaf_smem(int tile, int n, size_t esz) { return (64 + (size_t)tile * n) * esz; }
-static size_t reduce_smem(int fan, int n) { return (64 + (size_t)fan * n * n) * sizeof(double); }
+static int reg_class(int n) {
+  if (n <= 16) return (n + 1) & ~1;          // 2, 4, ..., 16
+  if (n <= 32) return (n + 3) & ~3;          // 20, 24, 28, 32
+  return 0;
+}
+
+static int reg_tile_of(int N) {
+  switch (N) {
+    case 2: return RegCfg<2>::TW; case 4: return RegCfg<4>::TW; case 6: return RegCfg<6>::TW;
+    case 8: return RegCfg<8>::TW; case 10: return RegCfg<10>::TW; case 12: return RegCfg<12>::TW;
+    case 14: return RegCfg<14>::TW; case 16: return RegCfg<16>::TW; case 20: return RegCfg<20>::TW;
+    case 24: return RegCfg<24>::TW; case 28: return RegCfg<28>::TW; default: return RegCfg<32>::TW;
+  }
+}
+
+static size_t cta_smem(int lda, int n, size_t esz) { return (64 + (size_t)lda * n) * esz; }
 
 void tsqr_plan_block(TsqrBlock& b, bool mixed) {
   const int n = b.n;
   const size_t esz = mixed ? sizeof(float) : sizeof(double);
-  // leaf tile: about 64 KB of shared memory, at least n rows, a multiple of 32
-  int64_t t = (int64_t)(64 * 1024 / (esz * n));
-  t = (t / 32) * 32;
-  if (t > 2048) t = 2048;
-  if (t < n) t = n;
-  if (t < 32) t = 32;
-  b.tile = (int)t;
-  int64_t f = (int64_t)(64 * 1024 / (sizeof(double) * (size_t)n * n));
-  if (f < 2) f = 2;
-  if (f > 256) f = 256;
-  b.fan = (int)f;
+  b.nreg = reg_class(n);
+  b.nw = 0;
+  if (b.nreg) {
+    b.wpc = 4;
+    b.tile = reg_tile_of(b.nreg);
+    // n <= 16: tree tiles fill a register tile (fan = TW / n >= 4); wider blocks reduce
+    // their trees with the block-per-tile kernel only, six triangles at a time
+    b.fan = b.nreg <= 16 ? b.tile / n : 6;
+  } else {
+    b.wpc = 0;
+    int64_t t = (int64_t)(64 * 1024 / (esz * n));
+    t = (t / 32) * 32;
+    if (t > 2048) t = 2048;
+    if (t < n) t = n;
+    if (t < 32) t = 32;
+    b.tile = (int)t;
+    int64_t f = (int64_t)(64 * 1024 / (sizeof(double) * (size_t)n * n));
+    if (f < 2) f = 2;
+    if (f > 256) f = 256;
+    b.fan = (int)f;
+  }
   int64_t tiles = (b.bound + b.tile - 1) / b.tile;
   int levels = 0;
   while (tiles > 1) {
@@ -185,59 +200,79 @@ int64_t tsqr_tri_elems(const TsqrBlock& b) {
 }
 
 int64_t tsqr_scratch_elems(const TsqrBlock& b, bool mixed) {
+  if (b.nreg) return 0;
   const size_t esz = mixed ? sizeof(float) : sizeof(double);
   int64_t need = 0;
-  const int64_t tiles = (b.bound + b.tile - 1) / b.tile;
-  if (leaf_smem(b.tile, b.n, esz) > kSmemCap) need = tiles * b.tile * b.n;
-  if (reduce_smem(b.fan, b.n) > kSmemCap) {
-    const int64_t rt = (tiles + b.fan - 1) / b.fan;
-    const int64_t r = rt * b.fan * b.n * b.n;
+  const int64_t grid = 152 * 2;
+  if (cta_smem(b.tile, b.n, esz) > kSmemCap) need = grid * b.tile * b.n;
+  if (cta_smem(b.fan * b.n, b.n, sizeof(double)) > kSmemCap) {
+    const int64_t r = grid * (int64_t)b.fan * b.n * b.n;
     if (r > need) need = r;
   }
   return need;
 }
 
 template <typename E>
-static void launch_leaf(const TsqrBlock& b, E* scratch, cudaStream_t st) {
-  const int64_t tiles = (b.bound + b.tile - 1) / b.tile;
-  if (tiles < 1) return;
-  size_t smem = leaf_smem(b.tile, b.n, sizeof(E));
-  if (smem > kSmemCap) smem = 64 * sizeof(E); else scratch = nullptr;
-  cudaFuncSetAttribute(k_tsqr_leaf<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_tsqr_leaf<E><<<(unsigned)tiles, kQrThreads, smem, st>>>(b, scratch);
+static void launch_cta(const TsqrBlock& b, const double* tri_in, double* tri_out, int64_t div_in, int64_t tiles,
+                       void* scratch, cudaStream_t st, int few_only = 0) {
+  const int lda = tri_in ? b.fan * b.n : b.tile;
+  size_t smem = cta_smem(lda, b.n, sizeof(E));
+  E* gs = nullptr;
+  if (smem > kSmemCap) {
+    smem = 64 * sizeof(E);
+    gs = static_cast<E*>(scratch);
+  }
+  cudaFuncSetAttribute(k_tsqr_cta<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int64_t blocks = tiles < 1 ? 1 : tiles;
+  const int64_t cap = 152 * 2;
+  if (blocks > cap) blocks = cap;
+  k_tsqr_cta<E><<<(unsigned)blocks, kQrThreads, smem, st>>>(b, tri_in, tri_out, div_in, gs, few_only);
 }
 
-void tsqr_leaf(const TsqrBlock& b, bool mixed, void* scratch, cudaStream_t st, int64_t* launches) {
-  if (mixed) launch_leaf<float>(b, static_cast<float*>(scratch), st);
-  else launch_leaf<double>(b, static_cast<double*>(scratch), st);
+void tsqr_leaf(const TsqrBlock& b, bool mixed, cudaStream_t st, int64_t* launches) {
+  void* scratch = b.scratch;
+  const int64_t tiles = (b.bound + b.tile - 1) / b.tile;
+  if (tiles < 1) return;
+  if (b.nreg) {
+    if (mixed) launch_reg_n<float>(b, nullptr, b.tri[0], 0, tiles, st);
+    else launch_reg_n<double>(b, nullptr, b.tri[0], 0, tiles, st);
+  } else if (mixed) {
+    launch_cta<float>(b, nullptr, b.tri[0], 0, tiles, scratch, st);
+  } else {
+    launch_cta<double>(b, nullptr, b.tri[0], 0, tiles, scratch, st);
+  }
   ++*launches;
 }
 
-void tsqr_reduce(TsqrBlock& b, void* scratch, cudaStream_t st, int64_t* launches) {
+void tsqr_reduce(TsqrBlock& b, cudaStream_t st, int64_t* launches) {
+  void* scratch = b.scratch;
   int64_t div = b.tile;
   int64_t tiles = (b.bound + b.tile - 1) / b.tile;
-  size_t smem = reduce_smem(b.fan, b.n);
-  double* gs = nullptr;
-  if (smem > kSmemCap) { smem = 64 * sizeof(double); gs = static_cast<double*>(scratch); }
-  cudaFuncSetAttribute(k_tsqr_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int cur = 0;
   for (int l = 0; l < b.levels; ++l) {
     const int64_t out_tiles = (tiles + b.fan - 1) / b.fan;
-    k_tsqr_reduce<<<(unsigned)out_tiles, kQrThreads, smem, st>>>(b, b.tri[cur], b.tri[cur ^ 1], div, gs);
-    ++*launches;
+    if (b.nreg && b.nreg <= 16) {
+      launch_reg_n<double>(b, b.tri[cur], b.tri[cur ^ 1], div, out_tiles, st);
+      launch_cta<double>(b, b.tri[cur], b.tri[cur ^ 1], div, out_tiles, scratch, st, 1);
+      *launches += 2;
+    } else {
+      launch_cta<double>(b, b.tri[cur], b.tri[cur ^ 1], div, out_tiles, scratch, st);
+      ++*launches;
+    }
     cur ^= 1;
     div *= b.fan;
     tiles = out_tiles;
   }
 }
 
-void tsqr_final(const TsqrBlock* blocks_dev, int n_blocks, int stack_rows, int N, double* stack,
-                double* R, int64_t ldr, cudaStream_t st, int64_t* launches) {
-  size_t smem = (64 + (size_t)stack_rows * N) * sizeof(double);
-  int use_smem = smem <= kSmemCap;
-  if (!use_smem) smem = 64 * sizeof(double);
-  cudaFuncSetAttribute(k_tsqr_final, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_tsqr_final<<<1, kQrThreads, smem, st>>>(blocks_dev, n_blocks, stack_rows, N, stack, R, ldr, use_smem);
+void tsqr_final(const TsqrBlock* blocks_dev, int n_blocks, TsqrBlock& stack_blk, double* R, int64_t ldr,
+                cudaStream_t st, int64_t* launches) {
+  const int N = stack_blk.n;
+  k_tsqr_stack<<<1, 256, 0, st>>>(blocks_dev, n_blocks, (int)stack_blk.M, N, const_cast<double*>(stack_blk.ptr));
+  ++*launches;
+  tsqr_leaf(stack_blk, false, st, launches);
+  tsqr_reduce(stack_blk, st, launches);
+  k_write_r<<<grid_for((int64_t)N * N, 256, 64), 256, 0, st>>>(stack_blk.tri[stack_blk.top], N, R, ldr);
   ++*launches;
 }
 
