@@ -88,6 +88,11 @@ struct figaro_plan_s {
   std::vector<cudaStream_t> side;      // one stream per R0 block: the TSQR chains run concurrently
   std::vector<cudaEvent_t> side_done;
   cudaEvent_t fork = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;  // captured R pipeline (see run_r)
+  cudaStream_t exec = nullptr;           // the plan's own stream: the graph runs here
+  cudaEvent_t join_in = nullptr, join_out = nullptr;
+  bool graph_failed = false;
+  int64_t graph_launches = 0;
   std::vector<cudaEvent_t> leaf_ev;    // stage timing: start/end of every block's leaf kernel
   double* Rtmp = nullptr;
   double* svdW = nullptr;
@@ -173,7 +178,7 @@ static void layout(figaro_plan_s& P, Arena& a) {
     b.hf = a.take<double>(M);
     b.heads = a.take<double>(M * std::max(n.N, 1));
     b.tails = a.take<double>(M * std::max(n.N, 1));
-    b.tails32 = nullptr;
+    b.tails32 = mixed ? a.take<float>(M * std::max(n.N, 1)) : nullptr;
     if (!n.leaf && !n.root) {
       b.data2 = a.take<double>(M * n.N_sub);
       b.gtails = a.take<double>(M * n.N_sub);
@@ -184,6 +189,8 @@ static void layout(figaro_plan_s& P, Arena& a) {
     b.tflag = a.take<uint8_t>(n.n_tiles * wide);
     b.tsum = a.take<double>(n.n_tiles * wide);
     b.tcarry = a.take<double>(n.n_tiles * wide);
+    b.lflag = a.take<uint8_t>(n.n_tiles * wide * 32);
+    b.lsum = a.take<double>(n.n_tiles * wide * 32);
     b.coldesc = a.take<int2>(std::max(n.N_sub, 1));
   }
   for (auto& blk : P.blocks) {
@@ -499,6 +506,7 @@ static void bind_blocks(figaro_plan_s& P) {
   for (auto& n : P.nodes) {
     if (n.N > 0) {
       P.blocks[bi].ptr = n.b.tails;
+      P.blocks[bi].ptr32 = n.b.tails32;
       P.blocks[bi].ld = n.M;
       P.blocks[bi].sizes = n.b.sizes;
       ++bi;
@@ -553,7 +561,7 @@ struct StageClock {
   }
 };
 
-static int run_r(figaro_plan_s& P, double* R, int64_t ldr) {
+static int enqueue_r(figaro_plan_s& P, double* R, int64_t ldr) {
   cudaStream_t st = P.st;
   const bool mixed = P.opt.precision == FIGARO_PREC_MIXED;
   P.launches = 0;
@@ -665,12 +673,15 @@ static int run_r(figaro_plan_s& P, double* R, int64_t ldr) {
     lp.beta = P.beta;
     lp.beta_len = P.beta_len;
     lp.tails = n.b.tails;
+    lp.tails32 = mixed ? n.b.tails32 : nullptr;
     lp.ldt = n.M;
     lp.heads = n.b.heads;
     lp.ldh = n.M;
     lp.tflag = n.b.tflag;
     lp.tsum = n.b.tsum;
     lp.tcarry = n.b.tcarry;
+    lp.lflag = n.b.lflag;
+    lp.lsum = n.b.lsum;
     lp.n_tiles = n.n_tiles;
     leaf_heads_tails(lp, st, &P.launches);
   }
@@ -704,6 +715,8 @@ static int run_r(figaro_plan_s& P, double* R, int64_t ldr) {
     gp.tflag = n.b.tflag;
     gp.tsum = n.b.tsum;
     gp.tcarry = n.b.tcarry;
+    gp.lflag = n.b.lflag;
+    gp.lsum = n.b.lsum;
     gp.n_tiles = n.n_tiles;
     gp.is_root = n.root;
     if (gp.N > 0) gen_heads_tails(gp, st, &P.launches);
@@ -711,25 +724,69 @@ static int run_r(figaro_plan_s& P, double* R, int64_t ldr) {
   clk.stop();
   // ---- stages 5-6: TSQR of every R0 block, each on its own stream (the blocks are
   // independent), then the final QR of their stacked triangles on the main stream.
-  // Stage 5 sums the leaf kernels' durations (timed on their own streams, so they may
-  // overlap); stage 6 is the wall time of the whole TSQR section.
+  // With stage timing the chains run one after another on the main stream instead, so
+  // that the leaf kernels' event times are not shared with concurrent work: stage 5 sums
+  // the leaf launches, stage 6 is the wall time of the whole TSQR section.
   clk.start(6);
   FIG_CUDA(cudaEventRecord(P.fork, st));
   for (size_t bi = 0; bi < P.blocks.size(); ++bi) {
-    cudaStream_t s = P.side[bi];
-    FIG_CUDA(cudaStreamWaitEvent(s, P.fork, 0));
+    cudaStream_t s = P.opt.stage_timing ? st : P.side[bi];
+    if (!P.opt.stage_timing) FIG_CUDA(cudaStreamWaitEvent(s, P.fork, 0));
     if (P.opt.stage_timing) FIG_CUDA(cudaEventRecord(P.leaf_ev[2 * bi], s));
     const int64_t l0 = P.launches;
     tsqr_leaf(P.blocks[bi], mixed, s, &P.launches);
     P.stage_launch[5] += P.launches - l0;
     if (P.opt.stage_timing) FIG_CUDA(cudaEventRecord(P.leaf_ev[2 * bi + 1], s));
     tsqr_reduce(P.blocks[bi], s, &P.launches);
-    FIG_CUDA(cudaEventRecord(P.side_done[bi], s));
-    FIG_CUDA(cudaStreamWaitEvent(st, P.side_done[bi], 0));
+    if (!P.opt.stage_timing) {
+      FIG_CUDA(cudaEventRecord(P.side_done[bi], s));
+      FIG_CUDA(cudaStreamWaitEvent(st, P.side_done[bi], 0));
+    }
   }
   tsqr_final(P.blocks_dev, (int)P.blocks.size(), P.stack_blk, R, ldr, st, &P.launches);
   clk.stop();
   FIG_CUDA(cudaGetLastError());
+  return FIGARO_OK;
+}
+
+// The whole R pipeline depends on the data only through device-side sizes, so it is
+// captured once into a CUDA graph (writing into the plan's R buffer) and replayed on every
+// later call; the ~100 small launches of a step then cost no host time.  Stage timing and
+// any capture failure (e.g. pageable host inputs) fall back to direct launches.
+static int run_r(figaro_plan_s& P, double* R, int64_t ldr) {
+  if (P.opt.stage_timing || P.graph_failed) return enqueue_r(P, R, ldr);
+  cudaStream_t user = P.st;
+  if (!P.graph_exec) {
+    // capture on the plan's own stream (the caller's may be the uncapturable legacy stream)
+    cudaGraph_t g = nullptr;
+    int rc = FIGARO_OK;
+    P.st = P.exec;
+    cudaError_t e = cudaStreamBeginCapture(P.exec, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      rc = enqueue_r(P, P.Rtmp, P.N);
+      e = cudaStreamEndCapture(P.exec, &g);
+    }
+    P.st = user;
+    if (e == cudaSuccess && rc == FIGARO_OK) e = cudaGraphInstantiate(&P.graph_exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess || rc != FIGARO_OK) {
+      cudaGetLastError();
+      P.graph_exec = nullptr;
+      P.graph_failed = true;
+      g_last_error.clear();
+      return enqueue_r(P, R, ldr);
+    }
+    P.graph_launches = P.launches;
+  }
+  FIG_CUDA(cudaEventRecord(P.join_in, user));
+  FIG_CUDA(cudaStreamWaitEvent(P.exec, P.join_in, 0));
+  FIG_CUDA(cudaGraphLaunch(P.graph_exec, P.exec));
+  FIG_CUDA(cudaEventRecord(P.join_out, P.exec));
+  FIG_CUDA(cudaStreamWaitEvent(user, P.join_out, 0));
+  P.launches = P.graph_launches;
+  if (R != P.Rtmp)
+    FIG_CUDA(cudaMemcpy2DAsync(R, ldr * sizeof(double), P.Rtmp, P.N * sizeof(double), P.N * sizeof(double), P.N,
+                               cudaMemcpyDeviceToDevice, user));
   return FIGARO_OK;
 }
 
@@ -802,6 +859,7 @@ const char* figaro_last_error(void) { return g_last_error.c_str(); }
 int figaro_plan_destroy(figaro_plan_t p) {
   if (!p) return FIGARO_OK;
   if (p->arena) cudaStreamSynchronize(p->st);
+  if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
   for (auto& e : p->ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : p->side_done)
@@ -809,6 +867,9 @@ int figaro_plan_destroy(figaro_plan_t p) {
   for (auto& e : p->leaf_ev)
     if (e) cudaEventDestroy(e);
   if (p->fork) cudaEventDestroy(p->fork);
+  if (p->join_in) cudaEventDestroy(p->join_in);
+  if (p->join_out) cudaEventDestroy(p->join_out);
+  if (p->exec) cudaStreamDestroy(p->exec);
   for (auto& s : p->side)
     if (s) cudaStreamDestroy(s);
   if (p->err_host) cudaFreeHost(p->err_host);
@@ -867,6 +928,9 @@ int figaro_plan(const figaro_join_tree* tree, const figaro_options* opt, void* s
     if (e != cudaSuccess) return bail(e, "cudaEventCreate");
   }
   e = cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->join_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->join_out, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->exec, cudaStreamNonBlocking);
   if (e != cudaSuccess) return bail(e, "cudaEventCreate");
   P->side.assign(P->blocks.size(), nullptr);
   P->side_done.assign(P->blocks.size(), nullptr);

@@ -1,0 +1,84 @@
+// Double-float arithmetic on the FP32 pipe: a value is an unevaluated sum hi + lo of two
+// floats (about 48 significant bits).  Used by the mixed-precision head/tail scans, which
+// must keep their prefix sums accurate without paying for FP64 instructions (GB300 runs
+// FP64 at 1/64 of the FP32 rate).
+//
+// Building blocks (published error-free transformations):
+//   two_sum   Knuth's TwoSum: s + e == a + b exactly (6 additions).
+//   fast_two  Dekker's Fast2Sum for |a| >= |b|: s + e == a + b exactly (3 additions).
+//   two_prod  FMA-based product: p + e == a * b exactly (Ogita, Rump, Oishi 2005).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fig {
+
+struct dfl {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void fast_two(float a, float b, float& s, float& e) {
+  s = a + b;
+  e = b - (s - a);
+}
+
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  e += a.lo + b.lo;
+  dfl r;
+  fast_two(s, e, r.hi, r.lo);
+  return r;
+}
+
+__device__ __forceinline__ dfl df_neg(dfl a) { return dfl{-a.hi, -a.lo}; }
+
+// a * b for a double-float a and a float b.
+__device__ __forceinline__ dfl df_mul_f(dfl a, float b) {
+  const float p = a.hi * b;
+  float e = fmaf(a.hi, b, -p);          // two_prod error
+  e = fmaf(a.lo, b, e);
+  dfl r;
+  fast_two(p, e, r.hi, r.lo);
+  return r;
+}
+
+// Exact split of a non-negative integer below 2^48 into hi + lo floats.
+__device__ __forceinline__ dfl df_from_count(int64_t p) {
+  const float h = (float)p;                       // rounds to 24 bits
+  const float l = (float)(p - (int64_t)h);        // remainder below 2^24 in magnitude: exact
+  return dfl{h, l};
+}
+
+// Split a double x into hi + lo with |x - hi - lo| <= 2^-46 |x| without FP64
+// instructions: hi takes the sign, the exponent and the leading 23 bits of the
+// mantissa (truncated), lo the remaining 29 bits rounded to a float and scaled by
+// 2^(e - 1075).  Outside |x| in [2^-74, 2^127] (zero, tiny or huge values) the FP64
+// conversion is used instead.
+__device__ __forceinline__ dfl df_from_double(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FFull);
+  if (e < 949 || e > 1150) {
+    if ((b << 1) == 0ull) return dfl{0.0f, 0.0f};
+    const float h = (float)x;
+    return dfl{h, (float)(x - (double)h)};
+  }
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  const float h = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)(m >> 29));
+  const float scale = __uint_as_float((unsigned)(e - 1075 + 127) << 23);   // 2^(e - 1075)
+  float l = (float)(unsigned)(m & 0x1FFFFFFFull) * scale;
+  if (sign) l = -l;
+  return dfl{h, l};
+}
+
+__device__ __forceinline__ double df_to_double(dfl a) { return (double)a.hi + (double)a.lo; }
+
+}  // namespace fig

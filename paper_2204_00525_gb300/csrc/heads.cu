@@ -5,9 +5,10 @@
 // hold a sixth of a relation, so here the sorted rows are cut into fixed tiles of
 // 256 elements per warp regardless of group boundaries.  Per column, a prefix sum that
 // restarts at every group start is computed in three steps: (1) every tile reports
-// whether it contains a group start and the sum after its last start, (2) one thread
-// block per column scans those tile aggregates into a carry per tile, (3) every tile recomputes its
-// prefix sums with the carry and writes tail rows and heads.
+// whether it contains a group start and the sum after its last start, and every lane its
+// exclusive (flag, sum) inside the tile, (2) one thread block per column scans the tile
+// aggregates into a carry per tile, (3) every lane starts its running sum at its carry and
+// writes tail rows and heads (one add, one FMA and one multiply per cell).
 //
 // Tail of a group with rows a_0..a_{m-1} (0-based position p, exclusive prefix S_p):
 //   row p >= 1:  sqrt(Phi_circ) (sqrt(p) a_p - S_p / sqrt(p)) / sqrt(p + 1)
@@ -20,6 +21,7 @@
 //   sqrt(Phi_up) (sqrt(W_k) D_k - v_k P_k / sqrt(W_k)) / sqrt(W_k + v_k^2)
 //   = gamma_k (W_k D_k - v_k P_k),  gamma_k = sqrt(Phi_up) / sqrt(W_k (W_k + v_k^2)),
 //   head: P_n / sqrt(W_n) with W_n = Phi_down(x_p).
+#include "dfloat.cuh"
 #include "kernels.cuh"
 
 namespace fig {
@@ -105,8 +107,8 @@ __global__ void __launch_bounds__(kCarryThreads) k_tile_carry(const uint8_t* tfl
 
 // ------------------------------------------------------------------ relations (v = 1)
 struct LeafRow {
-  int64_t src;   // input row
-  int64_t pos;   // position inside the group
+  int32_t src;   // input row
+  int32_t pos;   // position inside the group
   int32_t g;
   bool ok, last;
 };
@@ -115,12 +117,28 @@ __device__ __forceinline__ LeafRow leaf_row(const LeafParams& p, int64_t e) {
   LeafRow r;
   r.ok = e < p.M;
   if (!r.ok) { r.src = 0; r.pos = 1; r.g = 0; r.last = false; return r; }
-  r.src = p.perm ? (int64_t)p.perm[e] : e;
+  r.src = p.perm ? p.perm[e] : (int32_t)e;
   r.g = p.row_gid[e];
   const int32_t start = p.goff[r.g];
-  r.pos = e - start;
+  r.pos = (int32_t)(e - start);
   r.last = (e == (int64_t)p.goff[r.g + 1] - 1);
   return r;
+}
+
+// Pass 1: per tile and column, the tile aggregate (for the carry scan) and every lane's
+// exclusive (flag, sum) inside the tile, so that pass 3 needs no cross-lane work.
+__device__ __forceinline__ void store_lane_and_tile(int f, double s, int lane, int64_t slot, int64_t tslot,
+                                                    uint8_t* lflag, double* lsum, uint8_t* tflag, double* tsum) {
+  pair_scan_incl(f, s, lane);
+  int fe = __shfl_up_sync(0xffffffffu, f, 1);
+  double se = __shfl_up_sync(0xffffffffu, s, 1);
+  if (lane == 0) { fe = 0; se = 0.0; }
+  lflag[slot * 32 + lane] = (uint8_t)fe;
+  lsum[slot * 32 + lane] = se;
+  if (lane == 31) {
+    tflag[tslot] = (uint8_t)f;
+    tsum[tslot] = s;
+  }
 }
 
 __global__ void __launch_bounds__(256) k_leaf_agg(LeafParams p) {
@@ -138,60 +156,153 @@ __global__ void __launch_bounds__(256) k_leaf_agg(LeafParams p) {
 #pragma unroll
       for (int i = 0; i < kHtItems; ++i) {
         if (!rw[i].ok) continue;
-        const double x = p.data[rw[i].src * p.rs + (int64_t)c * p.cs];
+        const double x = p.data[(int64_t)rw[i].src * p.rs + (int64_t)c * p.cs];
         if (rw[i].pos == 0) { f = 1; s = x; } else { s += x; }
       }
-      pair_scan_incl(f, s, lane);
-      if (lane == 31) {
-        p.tflag[(int64_t)c * p.n_tiles + t] = (uint8_t)f;
-        p.tsum[(int64_t)c * p.n_tiles + t] = s;
-      }
+      const int64_t slot = (int64_t)c * p.n_tiles + t;
+      store_lane_and_tile(f, s, lane, slot, slot, p.lflag, p.lsum, p.tflag, p.tsum);
     }
   }
 }
 
-__global__ void __launch_bounds__(256) k_leaf_emit(LeafParams p) {
+// Pass 3: the running sum of every lane starts at its carry (tile carry combined with the
+// lane's exclusive partial), so each cell costs one add, one FMA and one multiply.
+__global__ void __launch_bounds__(256, 2) k_leaf_emit(LeafParams p) {
   const int lane = threadIdx.x & 31;
   const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t t = wid; t < p.n_tiles; t += nwarps) {
     const int64_t e0 = t * kHtTile + (int64_t)lane * kHtItems;
     LeafRow rw[kHtItems];
-    double gam[kHtItems];
+    double gam[kHtItems], pd[kHtItems];
 #pragma unroll
     for (int i = 0; i < kHtItems; ++i) {
       rw[i] = leaf_row(p, e0 + i);
-      gam[i] = (rw[i].ok && rw[i].pos > 0) ? p.sq_phic[rw[i].g] * beta_at(p.beta, p.beta_len, rw[i].pos) : 0.0;
+      const bool tail = rw[i].ok && rw[i].pos > 0;
+      gam[i] = tail ? p.sq_phic[rw[i].g] * beta_at(p.beta, p.beta_len, rw[i].pos) : 0.0;
+      pd[i] = (double)rw[i].pos;
     }
     for (int c = 0; c < p.N; ++c) {
-      double x[kHtItems], loc[kHtItems];
-      bool use_carry[kHtItems];
-      double run = 0.0;
-      int seen = 0;
-#pragma unroll
-      for (int i = 0; i < kHtItems; ++i) {
-        x[i] = rw[i].ok ? p.data[rw[i].src * p.rs + (int64_t)c * p.cs] : 0.0;
-        if (rw[i].ok && rw[i].pos == 0) { run = 0.0; seen = 1; }
-        loc[i] = run;
-        use_carry[i] = !seen;
-        run += x[i];
-      }
-      int fi = seen;
-      double si = run;
-      pair_scan_incl(fi, si, lane);
-      int fe = __shfl_up_sync(0xffffffffu, fi, 1);
-      double se = __shfl_up_sync(0xffffffffu, si, 1);
-      if (lane == 0) { fe = 0; se = 0.0; }
-      const double lane_carry = fe ? se : p.tcarry[(int64_t)c * p.n_tiles + t] + se;
+      const int64_t slot = (int64_t)c * p.n_tiles + t;
+      const int fe = p.lflag[slot * 32 + lane];
+      const double se = p.lsum[slot * 32 + lane];
+      double run = fe ? se : p.tcarry[slot] + se;
       double* tcol = p.tails + (int64_t)c * p.ldt;
+      double xs[kHtItems];                 // all loads first: the stores below may alias data
+#pragma unroll
+      for (int i = 0; i < kHtItems; ++i) xs[i] = rw[i].ok ? p.data[(int64_t)rw[i].src * p.rs + (int64_t)c * p.cs] : 0.0;
 #pragma unroll
       for (int i = 0; i < kHtItems; ++i) {
         if (!rw[i].ok) continue;
-        const double S = use_carry[i] ? lane_carry + loc[i] : loc[i];
-        if (rw[i].pos > 0)
-          tcol[e0 + i - rw[i].g - 1] = gam[i] * fma((double)rw[i].pos, x[i], -S);
-        if (rw[i].last)
-          p.heads[(int64_t)c * p.ldh + rw[i].g] = (S + x[i]) * p.hrow[rw[i].g];
+        const double x = xs[i];
+        if (rw[i].pos == 0) run = 0.0;
+        if (rw[i].pos > 0) tcol[e0 + i - rw[i].g - 1] = gam[i] * fma(pd[i], x, -run);
+        run += x;
+        if (rw[i].last) p.heads[(int64_t)c * p.ldh + rw[i].g] = run * p.hrow[rw[i].g];
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ mixed precision (v = 1)
+// Same three passes with the prefix sums in double-float arithmetic on the FP32 pipe: the
+// FP64 inputs are split exactly enough (2^-46) into float pairs, every running sum and
+// p a_p - S_p is formed in double-float, and the tail row is rounded once to float for
+// the FP32 TSQR leaf.  Heads stay float64.  Carries between lanes and tiles are kept in
+// float64 (one conversion per lane and column).
+__device__ __forceinline__ void pair_scan_incl_df(int& f, dfl& s, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int fo = __shfl_up_sync(0xffffffffu, f, o);
+    const float sh = __shfl_up_sync(0xffffffffu, s.hi, o);
+    const float sl = __shfl_up_sync(0xffffffffu, s.lo, o);
+    if (lane >= o) {
+      if (!f) s = df_add(dfl{sh, sl}, s);
+      f |= fo;
+    }
+  }
+}
+
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  dfl r;
+  fast_two(p, e, r.hi, r.lo);
+  return r;
+}
+
+__global__ void __launch_bounds__(256) k_leaf_agg_mx(LeafParams p) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t = wid; t < p.n_tiles; t += nwarps) {
+    const int64_t e0 = t * kHtTile + (int64_t)lane * kHtItems;
+    LeafRow rw[kHtItems];
+#pragma unroll
+    for (int i = 0; i < kHtItems; ++i) rw[i] = leaf_row(p, e0 + i);
+    for (int c = 0; c < p.N; ++c) {
+      double xs[kHtItems];
+#pragma unroll
+      for (int i = 0; i < kHtItems; ++i) xs[i] = rw[i].ok ? p.data[(int64_t)rw[i].src * p.rs + (int64_t)c * p.cs] : 0.0;
+      int f = 0;
+      dfl s{0.0f, 0.0f};
+#pragma unroll
+      for (int i = 0; i < kHtItems; ++i) {
+        if (!rw[i].ok) continue;
+        const dfl x = df_from_double(xs[i]);
+        if (rw[i].pos == 0) { f = 1; s = x; } else { s = df_add(s, x); }
+      }
+      pair_scan_incl_df(f, s, lane);
+      int fe = __shfl_up_sync(0xffffffffu, f, 1);
+      float eh = __shfl_up_sync(0xffffffffu, s.hi, 1), el = __shfl_up_sync(0xffffffffu, s.lo, 1);
+      if (lane == 0) { fe = 0; eh = 0.0f; el = 0.0f; }
+      const int64_t slot = (int64_t)c * p.n_tiles + t;
+      p.lflag[slot * 32 + lane] = (uint8_t)fe;
+      p.lsum[slot * 32 + lane] = df_to_double(dfl{eh, el});
+      if (lane == 31) {
+        p.tflag[slot] = (uint8_t)f;
+        p.tsum[slot] = df_to_double(s);
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256, 2) k_leaf_emit_mx(LeafParams p) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t = wid; t < p.n_tiles; t += nwarps) {
+    const int64_t e0 = t * kHtTile + (int64_t)lane * kHtItems;
+    LeafRow rw[kHtItems];
+    float gam[kHtItems];
+#pragma unroll
+    for (int i = 0; i < kHtItems; ++i) {
+      rw[i] = leaf_row(p, e0 + i);
+      const bool tail = rw[i].ok && rw[i].pos > 0;
+      gam[i] = tail ? (float)(p.sq_phic[rw[i].g] * beta_at(p.beta, p.beta_len, rw[i].pos)) : 0.0f;
+    }
+    for (int c = 0; c < p.N; ++c) {
+      const int64_t slot = (int64_t)c * p.n_tiles + t;
+      const int fe = p.lflag[slot * 32 + lane];
+      const double se = p.lsum[slot * 32 + lane];
+      dfl run = df_from_double(fe ? se : p.tcarry[slot] + se);
+      float* tcol = p.tails32 + (int64_t)c * p.ldt;
+      double xs[kHtItems];
+#pragma unroll
+      for (int i = 0; i < kHtItems; ++i) xs[i] = rw[i].ok ? p.data[(int64_t)rw[i].src * p.rs + (int64_t)c * p.cs] : 0.0;
+#pragma unroll
+      for (int i = 0; i < kHtItems; ++i) {
+        if (!rw[i].ok) continue;
+        const dfl x = df_from_double(xs[i]);
+        if (rw[i].pos == 0) run = dfl{0.0f, 0.0f};
+        if (rw[i].pos > 0) {
+          const dfl d = df_add(df_mul(x, df_from_count(rw[i].pos)), df_neg(run));
+          tcol[e0 + i - rw[i].g - 1] = gam[i] * (d.hi + d.lo);
+        }
+        run = df_add(run, x);
+        if (rw[i].last) p.heads[(int64_t)c * p.ldh + rw[i].g] = df_to_double(run) * p.hrow[rw[i].g];
       }
     }
   }
@@ -208,33 +319,32 @@ static unsigned ht_grid(int64_t n_tiles) {
 void leaf_heads_tails(const LeafParams& p, cudaStream_t st, int64_t* launches) {
   if (p.N == 0) return;
   const unsigned g = ht_grid(p.n_tiles);
-  k_leaf_agg<<<g, 256, 0, st>>>(p);
+  if (p.tails32) k_leaf_agg_mx<<<g, 256, 0, st>>>(p);
+  else k_leaf_agg<<<g, 256, 0, st>>>(p);
   k_tile_carry<<<p.N, kCarryThreads, 0, st>>>(p.tflag, p.tsum, p.tcarry, p.n_tiles, nullptr);
-  k_leaf_emit<<<g, 256, 0, st>>>(p);
+  if (p.tails32) k_leaf_emit_mx<<<g, 256, 0, st>>>(p);
+  else k_leaf_emit<<<g, 256, 0, st>>>(p);
   *launches += 3;
 }
 
 // ------------------------------------------------------------------ join + projection
 struct GenRow {
-  int32_t g, pg, trow;
-  int64_t k;       // position inside the X_p group
-  double v, W, gam;
+  int32_t g, pg, trow, k;   // group, X_p group, output row, position inside the X_p group
+  double v;                 // weight sqrt(Theta_down)
   bool ok, last;
 };
 
 __device__ __forceinline__ GenRow gen_row(const GenParams& p, int64_t e, int64_t G) {
   GenRow r;
   r.ok = e < G;
-  if (!r.ok) { r.g = 0; r.pg = 0; r.trow = 0; r.k = 1; r.v = r.W = r.gam = 0.0; r.last = false; return r; }
+  if (!r.ok) { r.g = 0; r.pg = 0; r.trow = 0; r.k = 1; r.v = 0.0; r.last = false; return r; }
   r.g = (int32_t)e;
   r.pg = p.g2p[e];
   const int32_t start = p.pgoff[r.pg];
-  r.k = e - start;
+  r.k = (int32_t)(e - start);
   r.last = (e == (int64_t)p.pgoff[r.pg + 1] - 1);
   r.trow = (int32_t)(e - r.pg - 1);
   r.v = p.vw[e * 3 + 0];
-  r.W = p.vw[e * 3 + 1];
-  r.gam = p.vw[e * 3 + 2];
   return r;
 }
 
@@ -274,16 +384,15 @@ __global__ void __launch_bounds__(256) k_gen_agg(GenParams p) {
         const double x = rw[i].v * join_value(p, rw[i].g, d);
         if (rw[i].k == 0) { f = 1; s = x; } else { s += x; }
       }
-      pair_scan_incl(f, s, lane);
-      if (lane == 31) {
-        p.tflag[(int64_t)c * p.n_tiles + t] = (uint8_t)f;
-        p.tsum[(int64_t)c * p.n_tiles + t] = s;
-      }
+      const int64_t slot = (int64_t)c * p.n_tiles + t;
+      store_lane_and_tile(f, s, lane, slot, slot, p.lflag, p.lsum, p.tflag, p.tsum);
     }
   }
 }
 
-__global__ void __launch_bounds__(256) k_gen_emit(GenParams p) {
+// Generalized tail gamma (W D - v P) = (gamma W) D - (gamma v) P with P the running sum
+// of v D over the earlier groups of the same x_p.
+__global__ void __launch_bounds__(256, 2) k_gen_emit(GenParams p) {
   const int lane = threadIdx.x & 31;
   const int64_t G = p.sizes[0];
   const int64_t nt = (G + kHtTile - 1) / kHtTile;
@@ -292,37 +401,32 @@ __global__ void __launch_bounds__(256) k_gen_emit(GenParams p) {
   for (int64_t t = wid; t < nt; t += nwarps) {
     const int64_t e0 = t * kHtTile + (int64_t)lane * kHtItems;
     GenRow rw[kHtItems];
+    double gw[kHtItems], gv[kHtItems];
 #pragma unroll
-    for (int i = 0; i < kHtItems; ++i) rw[i] = gen_row(p, e0 + i, G);
+    for (int i = 0; i < kHtItems; ++i) {
+      rw[i] = gen_row(p, e0 + i, G);
+      const double W = rw[i].ok ? p.vw[(int64_t)rw[i].g * 3 + 1] : 0.0;
+      const double gam = rw[i].ok ? p.vw[(int64_t)rw[i].g * 3 + 2] : 0.0;
+      gw[i] = gam * W;
+      gv[i] = gam * rw[i].v;
+    }
     for (int c = 0; c < p.N; ++c) {
       const int2 d = p.coldesc[c];
-      double D[kHtItems], loc[kHtItems];
-      bool use_carry[kHtItems];
-      double run = 0.0;
-      int seen = 0;
+      const int64_t slot = (int64_t)c * p.n_tiles + t;
+      const int fe = p.lflag[slot * 32 + lane];
+      const double se = p.lsum[slot * 32 + lane];
+      double run = fe ? se : p.tcarry[slot] + se;
+      double Ds[kHtItems];                 // all loads first: the stores below may alias the sources
 #pragma unroll
-      for (int i = 0; i < kHtItems; ++i) {
-        D[i] = rw[i].ok ? join_value(p, rw[i].g, d) : 0.0;
-        if (rw[i].ok && rw[i].k == 0) { run = 0.0; seen = 1; }
-        loc[i] = run;
-        use_carry[i] = !seen;
-        run += rw[i].v * D[i];
-      }
-      int fi = seen;
-      double si = run;
-      pair_scan_incl(fi, si, lane);
-      int fe = __shfl_up_sync(0xffffffffu, fi, 1);
-      double se = __shfl_up_sync(0xffffffffu, si, 1);
-      if (lane == 0) { fe = 0; se = 0.0; }
-      const double lane_carry = fe ? se : p.tcarry[(int64_t)c * p.n_tiles + t] + se;
+      for (int i = 0; i < kHtItems; ++i) Ds[i] = rw[i].ok ? join_value(p, rw[i].g, d) : 0.0;
 #pragma unroll
       for (int i = 0; i < kHtItems; ++i) {
         if (!rw[i].ok) continue;
-        const double P = use_carry[i] ? lane_carry + loc[i] : loc[i];
-        if (rw[i].k > 0)
-          p.gtails[(int64_t)c * p.M + rw[i].trow] = rw[i].gam * fma(rw[i].W, D[i], -rw[i].v * P);
-        if (rw[i].last)
-          p.data2[(int64_t)c * p.M + rw[i].pg] = fma(rw[i].v, D[i], P) * p.hf[rw[i].pg];
+        const double D = Ds[i];
+        if (rw[i].k == 0) run = 0.0;
+        if (rw[i].k > 0) p.gtails[(int64_t)c * p.M + rw[i].trow] = fma(gw[i], D, -gv[i] * run);
+        run = fma(rw[i].v, D, run);
+        if (rw[i].last) p.data2[(int64_t)c * p.M + rw[i].pg] = run * p.hf[rw[i].pg];
       }
     }
   }

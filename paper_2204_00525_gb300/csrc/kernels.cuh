@@ -57,6 +57,8 @@ struct NodeBuf {
   uint8_t* tflag;       // [n_tiles * max(N_i, N_sub)]
   double* tsum;
   double* tcarry;
+  uint8_t* lflag;       // [n_tiles * max(N_i, N_sub) * 32]: lane exclusive partials
+  double* lsum;
   int2* coldesc;        // [N_sub] (source kind, source column) for the join
 };
 
@@ -133,11 +135,14 @@ struct LeafParams {
   int64_t beta_len;
   double* tails;
   int64_t ldt;
+  float* tails32;            // mixed precision: float tails (leading dimension ldt) instead of tails
   double* heads;
   int64_t ldh;
   uint8_t* tflag;
   double* tsum;
   double* tcarry;
+  uint8_t* lflag;
+  double* lsum;
   int64_t n_tiles;
 };
 
@@ -163,6 +168,8 @@ struct GenParams {
   uint8_t* tflag;
   double* tsum;
   double* tcarry;
+  uint8_t* lflag;
+  double* lsum;
   int64_t n_tiles;
   int is_root;
 };
@@ -176,6 +183,7 @@ enum BlockKind : int { BLK_TAILS = 0, BLK_GEN = 1, BLK_ROOT = 2, BLK_FIXED = 3 }
 
 struct TsqrBlock {
   const double* ptr;         // col-major, leading dimension ld
+  const float* ptr32;        // mixed-precision tails: float rows in place of ptr
   int64_t ld;
   int n;                     // columns
   int kind;

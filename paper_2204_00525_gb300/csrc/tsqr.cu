@@ -31,21 +31,27 @@ template <typename E>
 __device__ void hh_qr(E* A, int lda, int m, int n, E* red) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const int kmax = m < n ? m : n;
+  // red[0..32]: block_sum scratch; red[40..42]: the step's scalars (computed by one lane:
+  // FP64 square roots and divisions cost some twenty FMA slots each on this part)
   for (int k = 0; k < kmax; ++k) {
     E* ak = A + (int64_t)k * lda;
     E s = 0;
     for (int i = k + 1 + tid; i < m; i += blockDim.x) s = fma(ak[i], ak[i], s);
     s = block_sum<E>(s, red);
-    const E alpha = ak[k];
-    if (s == E(0)) continue;
-    const E normx = sqrt(fma(alpha, alpha, s));
-    const E beta = alpha >= E(0) ? -normx : normx;
-    const E tau = (beta - alpha) / beta;
-    const E scal = E(1) / (alpha - beta);
+    if (s == E(0)) continue;                        // uniform: column already reduced
+    if (tid == 0) {
+      const E alpha = ak[k];
+      const E normx = sqrt(fma(alpha, alpha, s));
+      const E beta = alpha >= E(0) ? -normx : normx;
+      red[40] = (beta - alpha) / beta;                // tau
+      red[41] = E(1) / (alpha - beta);                // scale of v (v_k = 1)
+      red[42] = beta;
+    }
     __syncthreads();
-    for (int i = k + 1 + tid; i < m; i += blockDim.x) ak[i] *= scal;   // v, with v_k = 1
-    if (tid == 0) ak[k] = beta;
+    const E tau = red[40], scal = red[41];
+    for (int i = k + 1 + tid; i < m; i += blockDim.x) ak[i] *= scal;
     __syncthreads();
+    if (tid == 0) ak[k] = red[42];
     for (int j = k + 1 + warp; j < n; j += nw) {
       E* aj = A + (int64_t)j * lda;
       const E ajk = aj[k];
@@ -71,7 +77,7 @@ __global__ void __launch_bounds__(kQrThreads) k_tsqr_cta(TsqrBlock b, const doub
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int64_t rows = block_rows(b);
   if (copy_single(b, rows, div_in, tri_in, tri_out)) return;
-  if (few_only && level_tiles(b, rows, div_in, false) >= kWarpModeTiles) return;
+  if (few_only && level_tiles(b, rows, div_in, tri_in == nullptr) >= kWarpModeTiles) return;
   const int n = b.n;
   const int lda = tri_in ? b.fan * n : b.tile;
   E* red = reinterpret_cast<E*>(smem_raw);
@@ -85,7 +91,8 @@ __global__ void __launch_bounds__(kQrThreads) k_tsqr_cta(TsqrBlock b, const doub
       m = (int)((rows - r0) < b.tile ? (rows - r0) : b.tile);
       for (int c = 0; c < n; ++c)
         for (int i = threadIdx.x; i < m; i += blockDim.x)
-          A[(int64_t)c * lda + i] = (E)b.ptr[(int64_t)c * b.ld + r0 + i];
+          A[(int64_t)c * lda + i] = b.ptr32 ? (E)b.ptr32[(int64_t)c * b.ld + r0 + i]
+                                            : (E)b.ptr[(int64_t)c * b.ld + r0 + i];
     } else {
       const int64_t first = t * b.fan;
       const int cnt = (int)((nt_in - first) < b.fan ? (nt_in - first) : b.fan);
@@ -234,8 +241,14 @@ void tsqr_leaf(const TsqrBlock& b, bool mixed, cudaStream_t st, int64_t* launche
   const int64_t tiles = (b.bound + b.tile - 1) / b.tile;
   if (tiles < 1) return;
   if (b.nreg) {
-    if (mixed) launch_reg_n<float>(b, nullptr, b.tri[0], 0, tiles, st);
-    else launch_reg_n<double>(b, nullptr, b.tri[0], 0, tiles, st);
+    if (mixed) {
+      launch_reg_n<float>(b, nullptr, b.tri[0], 0, tiles, st);
+      launch_cta<float>(b, nullptr, b.tri[0], 0, tiles, scratch, st, 1);
+    } else {
+      launch_reg_n<double>(b, nullptr, b.tri[0], 0, tiles, st);
+      launch_cta<double>(b, nullptr, b.tri[0], 0, tiles, scratch, st, 1);
+    }
+    ++*launches;
   } else if (mixed) {
     launch_cta<float>(b, nullptr, b.tri[0], 0, tiles, scratch, st);
   } else {

@@ -144,9 +144,10 @@ struct RegQR<E, N, RPL, N> {
   __device__ __forceinline__ static void run(E (&)[RPL][N], int, int) {}
 };
 
-// Tree levels run two kernels: this one (one warp per tile) works only when the level has
-// at least kWarpModeTiles tiles; the block-per-tile kernel takes the levels with fewer
-// tiles, where the latency of one warp's QR would dominate.
+// Every level (leaf or tree) of a block with <= 32 columns runs two kernels: this one (one
+// warp per tile) works only when the level has at least kWarpModeTiles tiles; the
+// block-per-tile kernel takes the levels with fewer tiles, where the latency of one
+// warp's QR would dominate.
 constexpr int64_t kWarpModeTiles = 152 * 4;
 
 template <typename E, int N>
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(128) k_tsqr_reg(TsqrBlock b, const double* tri
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t nt_in = tri_in ? (rows + div_in - 1) / div_in : 0;
   const int64_t n_tiles = level_tiles(b, rows, div_in, tri_in == nullptr);
-  if (tri_in && n_tiles < kWarpModeTiles) return;     // the block-per-tile kernel takes it
+  if (n_tiles < kWarpModeTiles) return;               // the block-per-tile kernel takes it
   for (int64_t t = gw; t < n_tiles; t += nw) {
     E a[RPL][N];
     int m;
@@ -172,7 +173,8 @@ __global__ void __launch_bounds__(128) k_tsqr_reg(TsqrBlock b, const double* tri
         const int i = lane + 32 * r;
 #pragma unroll
         for (int c = 0; c < N; ++c)
-          a[r][c] = (i < m && c < n) ? (E)b.ptr[(int64_t)c * b.ld + r0 + i] : E(0);
+          a[r][c] = (i < m && c < n) ? (b.ptr32 ? (E)b.ptr32[(int64_t)c * b.ld + r0 + i]
+                                                : (E)b.ptr[(int64_t)c * b.ld + r0 + i]) : E(0);
       }
     } else {
       const int64_t first = t * b.fan;

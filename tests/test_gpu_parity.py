@@ -343,3 +343,20 @@ def test_mixed_precision_small_cases():
         R = gpu_r(db, precision=binding.FIGARO_PREC_MIXED)
         G = ogr.factorized_gram(orl.full_reduce(db))
         assert rel_err(R.T @ R, G) < TOL_MIXED
+
+
+def test_mixed_heads_are_double_float_accurate():
+    """The mixed path forms its group sums in double-float arithmetic (about 46 bits):
+    the heads H(S^x) it passes to the join must agree with the oracle's float64 heads far
+    below float32 precision."""
+    from paper_2204_00525_gb300 import binding
+    db = orl.full_reduce(synth.path3(rows=50_000, keys=200))
+    p = plan_for(db, precision=binding.FIGARO_PREC_MIXED)
+    p.qr_r()
+    for i, rel in enumerate(db.relations):
+        order, starts, _ = orl.group_rows(orl.key_columns(rel, orl.sort_attrs(db, i)))
+        heads_o = np.concatenate([ogv.head(rel.data[order[starts[g]:starts[g + 1]]])
+                                  for g in range(len(starts) - 1)])
+        h = p.debug(i, "heads", np.float64).reshape(rel.n_data, -1).T
+        close(h, heads_o, tol=1e-12)
+    p.close()
