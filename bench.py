@@ -196,6 +196,12 @@ def run_figaro(args):
     G64 = R64.T @ R64
     err_mx = float(np.linalg.norm(Rmx.T @ Rmx - G64) / np.linalg.norm(G64))
     pmx.close()
+    pmxs = binding.JoinPlan(dev_inputs, db.parent, precision=binding.FIGARO_PREC_MIXED, stage_timing=True,
+                            stream=stream)
+    pmxs._R = torch.empty(db.n_cols, db.n_cols, dtype=torch.float64, device="cuda")
+    time_steps(pmxs, torch, args.steps, args.warmup, barrier)
+    mx_stages = {k: v[0] / args.steps for k, v in pmxs.stage_times().items()}
+    pmxs.close()
 
     # --- end to end through the C ABI with pinned host buffers
     host_inputs = make_inputs(db, torch, "cpu")
@@ -238,7 +244,8 @@ def run_figaro(args):
                    "parallelism": f"replicas x{world} (independent instances)"},
         "gbs": gbs, "hbm_frac": gbs / hbm, "hbm_peak_gbs": hbm, "hbm_peak_kind": hbm_kind,
         "mixed": {"ms_per_step": msmx, "value": cells * world / (msmx * 1e-3), "speedup_vs_fp64": ms64 / msmx,
-                  "rel_err_RtR_vs_fp64_path": err_mx, "dtype": "f32 TSQR leaves, f64 elsewhere"},
+                  "rel_err_RtR_vs_fp64_path": err_mx, "stages_ms_per_step": mx_stages,
+                  "dtype": "double-float head/tail sums, f32 tails and TSQR leaf/tree, f64 counts, join, final QR"},
         "stages_ms_per_step": per_stage,
         "stage_note": "from a stage-timed plan with serialised TSQR chains; tsqr_tree = whole TSQR section, tsqr_leaf = its leaf launches",
         "r0_rows": info["r0_rows"],

@@ -91,8 +91,10 @@ typedef struct figaro_join_tree {
 
 /* Options.  Initialise with figaro_default_options.
  *   precision        FIGARO_PREC_FP64: every step in float64.  FIGARO_PREC_MIXED:
- *                    counts exact, head/tail scans in float64, the TSQR leaf tiles in
- *                    float32 on equilibrated columns, the TSQR tree and R in float64.
+ *                    counts exact; head/tail prefix sums in double-float arithmetic
+ *                    (two floats, about 46 bits) with float32 tail rows; the TSQR leaf
+ *                    tiles and tree levels of every R0 block in float32; the final QR
+ *                    of the stacked block triangles, R, SVD and PCA in float64.
  *   presorted        1: every relation is already sorted by its key (the order §5
  *                    assumes: attributes shared with the parent first, then the rest,
  *                    each part in ascending attribute id, values ascending); the sort

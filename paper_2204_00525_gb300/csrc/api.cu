@@ -138,9 +138,9 @@ static void layout(figaro_plan_s& P, Arena& a) {
   P.err_dev = a.take<int>(4);
   P.beta_len = std::min<int64_t>(maxM + 1, kBetaMax);
   P.beta = a.take<double>(P.beta_len);
-  const int64_t rt = radix_tiles(maxM);
-  P.radix_hist = a.take<int32_t>(2 * 256 * rt);
-  P.radix_scan_tmp = a.take<int32_t>(scan_tmp_elems(256 * rt));
+  const int64_t rh = radix_hist_elems(maxM);
+  P.radix_hist = a.take<int32_t>(2 * rh);
+  P.radix_scan_tmp = a.take<int32_t>(scan_tmp_elems(rh));
   for (auto& n : P.nodes) {
     NodeBuf& b = n.b;
     const int64_t M = n.M;
@@ -737,7 +737,7 @@ static int enqueue_r(figaro_plan_s& P, double* R, int64_t ldr) {
     tsqr_leaf(P.blocks[bi], mixed, s, &P.launches);
     P.stage_launch[5] += P.launches - l0;
     if (P.opt.stage_timing) FIG_CUDA(cudaEventRecord(P.leaf_ev[2 * bi + 1], s));
-    tsqr_reduce(P.blocks[bi], s, &P.launches);
+    tsqr_reduce(P.blocks[bi], mixed, s, &P.launches);
     if (!P.opt.stage_timing) {
       FIG_CUDA(cudaEventRecord(P.side_done[bi], s));
       FIG_CUDA(cudaStreamWaitEvent(st, P.side_done[bi], 0));
@@ -896,6 +896,16 @@ int figaro_plan(const figaro_join_tree* tree, const figaro_options* opt, void* s
   }
   P->st = static_cast<cudaStream_t>(stream);
   int rc = build(*P, tree);
+  if (rc == FIGARO_OK) {
+    // per-function shared-memory limits, raised once to the largest size any launch uses
+    cudaError_t e = keys_set_attributes();
+    if (e == cudaSuccess) e = tsqr_set_attributes();
+    if (e == cudaSuccess) e = svd_set_attributes();
+    if (e != cudaSuccess) {
+      delete P;
+      return fail(FIGARO_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+    }
+  }
   if (rc != FIGARO_OK) { delete P; return rc; }
   if (cudaGetDevice(&P->device) != cudaSuccess) {
     delete P;

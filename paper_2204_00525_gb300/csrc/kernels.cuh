@@ -67,6 +67,8 @@ void launch_minmax(const void* col, int key_type, int64_t n, long long* dmin, lo
 void launch_pack(const PackParams& p, int64_t n, uint64_t* key, int32_t* perm, int* err,
                  cudaStream_t st, int64_t* launches);
 int64_t radix_tiles(int64_t n);
+int64_t radix_hist_elems(int64_t n);
+cudaError_t keys_set_attributes();
 int radix_sort(uint64_t* key[2], int32_t* perm[2], int64_t n, int bits, int32_t* hist, int32_t* scan_tmp,
                cudaStream_t st, int64_t* launches);
 void segment(NodeBuf& b, int64_t n, int rest_bits, cudaStream_t st, int64_t* launches);
@@ -206,13 +208,15 @@ void tsqr_plan_block(TsqrBlock& b, bool mixed);
 int64_t tsqr_tri_elems(const TsqrBlock& b);
 int64_t tsqr_scratch_elems(const TsqrBlock& b, bool mixed);
 void tsqr_leaf(const TsqrBlock& b, bool mixed, cudaStream_t st, int64_t* launches);
-void tsqr_reduce(TsqrBlock& b, cudaStream_t st, int64_t* launches);
+void tsqr_reduce(TsqrBlock& b, bool mixed, cudaStream_t st, int64_t* launches);
 void tsqr_final(const TsqrBlock* blocks_dev, int n_blocks, TsqrBlock& stack_blk, double* R, int64_t ldr,
                 cudaStream_t st, int64_t* launches);
 double tsqr_leaf_flops(int64_t rows, int n);
+cudaError_t tsqr_set_attributes();
 
 // ------------------------------------------------------------------ svd.cu
 size_t jacobi_smem(int N);
+cudaError_t svd_set_attributes();
 void jacobi_svd(const double* R, int64_t ldr, int N, double* W, double* V, double* sigma,
                 double* Vout, int* err, cudaStream_t st, int64_t* launches);
 void square_values(const double* s, double* out, int k, cudaStream_t st, int64_t* launches);

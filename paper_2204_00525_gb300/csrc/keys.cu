@@ -78,33 +78,45 @@ __global__ void k_check_sorted(const uint64_t* key, int64_t n, int* err) {
 }
 
 // ------------------------------------------------------------------ radix sort
-// One pass sorts by an 8-bit digit.  A tile is 8 warps x 8 rounds x 32 keys; inside a
-// tile keys keep their order (warps, rounds and lanes follow key order), so the sort
-// is stable.  hist is digit-major: hist[d * n_tiles + tile].
+// LSD radix sort by digits of up to 11 bits (a relation's packed key of b bits takes
+// ceil(b / 11) passes).  One pass: per-tile digit histograms (digit-major, so that one
+// exclusive scan yields every tile's output offset per digit), then a stable scatter.
+// A tile is 8 warps x 8 rounds x 32 keys; inside a tile keys keep their order (warps,
+// rounds and lanes follow key order), so the sort is stable.  Histogram and rank use
+// __match_any_sync so that equal digits in a warp (frequent with skewed keys) cost one
+// shared-memory update per distinct digit instead of one per key.
 constexpr int kRsWarps = 8, kRsRounds = 8;
 constexpr int kRsTile = kRsWarps * kRsRounds * 32;   // 2048 keys
+constexpr int kRsMaxBits = 11;
+constexpr int kRsMaxBins = 1 << kRsMaxBits;
 
-__global__ void __launch_bounds__(256) k_radix_hist(const uint64_t* key, int64_t n, int shift,
+__global__ void __launch_bounds__(256) k_radix_hist(const uint64_t* key, int64_t n, int shift, int bins,
                                                     int32_t* hist, int64_t n_tiles) {
-  __shared__ int32_t h[256];
-  h[threadIdx.x] = 0;
+  __shared__ int32_t h[kRsMaxBins];
+  for (int d = threadIdx.x; d < bins; d += 256) h[d] = 0;
   __syncthreads();
+  const unsigned mask = (unsigned)bins - 1u;
+  const int lane = threadIdx.x & 31;
   const int64_t base = (int64_t)blockIdx.x * kRsTile;
   for (int i = threadIdx.x; i < kRsTile; i += 256) {
-    int64_t e = base + i;
-    if (e < n) atomicAdd(&h[(key[e] >> shift) & 255u], 1);
+    const int64_t e = base + i;
+    const bool ok = e < n;
+    const unsigned d = ok ? (unsigned)(key[e] >> shift) & mask : (unsigned)kRsMaxBins + lane;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    if (ok && lane == __ffs(peers) - 1) atomicAdd(&h[d], __popc(peers));
   }
   __syncthreads();
-  hist[(int64_t)threadIdx.x * n_tiles + blockIdx.x] = h[threadIdx.x];
+  for (int d = threadIdx.x; d < bins; d += 256) hist[(int64_t)d * n_tiles + blockIdx.x] = h[d];
 }
 
 __global__ void __launch_bounds__(256) k_radix_scatter(const uint64_t* key_in, const int32_t* val_in,
                                                        uint64_t* key_out, int32_t* val_out,
-                                                       int64_t n, int shift, const int32_t* off,
+                                                       int64_t n, int shift, int bins, const int32_t* off,
                                                        int64_t n_tiles) {
-  __shared__ int32_t cnt[kRsWarps][256];
+  extern __shared__ int32_t cnt[];                    // [kRsWarps][bins]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int d = lane; d < 256; d += 32) cnt[warp][d] = 0;
+  const unsigned mask = (unsigned)bins - 1u;
+  for (int d = lane; d < bins; d += 32) cnt[warp * bins + d] = 0;
   __syncwarp();
   const int64_t base = (int64_t)blockIdx.x * kRsTile + (int64_t)warp * (kRsRounds * 32);
   uint64_t k[kRsRounds];
@@ -113,36 +125,34 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const uint64_t* key_in, c
   const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
   for (int j = 0; j < kRsRounds; ++j) {
-    int64_t e = base + j * 32 + lane;
-    bool ok = e < n;
+    const int64_t e = base + j * 32 + lane;
+    const bool ok = e < n;
     k[j] = ok ? key_in[e] : 0ull;
     v[j] = ok ? val_in[e] : 0;
-    unsigned d = ok ? (unsigned)((k[j] >> shift) & 255u) : 256u + lane;   // unique sentinel
-    unsigned peers = __match_any_sync(0xffffffffu, d);
-    int before = ok ? cnt[warp][d] : 0;
+    const unsigned d = ok ? (unsigned)(k[j] >> shift) & mask : (unsigned)kRsMaxBins + lane;   // unique sentinel
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const int before = ok ? cnt[warp * bins + d] : 0;
     __syncwarp();
-    if (ok && (peers & lt) == 0) cnt[warp][d] = before + __popc(peers);
+    if (ok && (peers & lt) == 0) cnt[warp * bins + d] = before + __popc(peers);
     __syncwarp();
     rank[j] = before + __popc(peers & lt);
   }
   __syncthreads();
-  // exclusive scan over warps for every digit
-  {
-    int d = threadIdx.x;
+  for (int d = threadIdx.x; d < bins; d += 256) {      // exclusive scan over warps per digit
     int run = 0;
     for (int w = 0; w < kRsWarps; ++w) {
-      int c = cnt[w][d];
-      cnt[w][d] = run;
+      const int c = cnt[w * bins + d];
+      cnt[w * bins + d] = run;
       run += c;
     }
   }
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < kRsRounds; ++j) {
-    int64_t e = base + j * 32 + lane;
+    const int64_t e = base + j * 32 + lane;
     if (e < n) {
-      unsigned d = (unsigned)((k[j] >> shift) & 255u);
-      int64_t dst = (int64_t)off[(int64_t)d * n_tiles + blockIdx.x] + cnt[warp][d] + rank[j];
+      const unsigned d = (unsigned)(k[j] >> shift) & mask;
+      const int64_t dst = (int64_t)off[(int64_t)d * n_tiles + blockIdx.x] + cnt[warp * bins + d] + rank[j];
       key_out[dst] = k[j];
       val_out[dst] = v[j];
     }
@@ -157,20 +167,32 @@ __global__ void k_radix_excl(const int32_t* counts, int32_t* incl, int64_t n) {
 
 int64_t radix_tiles(int64_t n) { return (n + kRsTile - 1) / kRsTile; }
 
-// Sorts (key, perm) in place by the low `bits` bits using ping-pong buffers; returns
-// which buffer (0 or 1) holds the result.
+// The dynamic shared-memory limit is a property of the function, not of a launch: it is
+// raised once to the largest size any launch uses (also inside captured graphs).
+cudaError_t keys_set_attributes() {
+  return cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(kRsWarps * kRsMaxBins * sizeof(int32_t)));
+}
+int64_t radix_hist_elems(int64_t n) { return (int64_t)kRsMaxBins * radix_tiles(n); }
+
+// Sorts (key, perm) by the low `bits` bits using ping-pong buffers; returns which buffer
+// (0 or 1) holds the result.
 int radix_sort(uint64_t* key[2], int32_t* perm[2], int64_t n, int bits, int32_t* hist, int32_t* scan_tmp,
                cudaStream_t st, int64_t* launches) {
   int cur = 0;
   const int64_t nt = radix_tiles(n);
-  for (int shift = 0; shift < bits; shift += 8) {
-    k_radix_hist<<<(unsigned)nt, 256, 0, st>>>(key[cur], n, shift, hist, nt);
+  const int passes = (bits + kRsMaxBits - 1) / kRsMaxBits;
+  const int width = (bits + passes - 1) / passes;
+  const int bins = 1 << width;
+  const int64_t hn = (int64_t)bins * nt;
+  const size_t smem = (size_t)kRsWarps * bins * sizeof(int32_t);
+  for (int shift = 0; shift < bits; shift += width) {
+    k_radix_hist<<<(unsigned)nt, 256, 0, st>>>(key[cur], n, shift, bins, hist, nt);
     ScanSrc src{SCAN_PLAIN_I32, hist, 0};
-    // inclusive scan in place, then the scatter uses exclusive offsets = incl - own
-    scan_inclusive<int32_t>(src, hist + 256 * nt, 256 * nt, nullptr, scan_tmp, st, launches);
-    k_radix_excl<<<grid_for(256 * nt, 256), 256, 0, st>>>(hist, hist + 256 * nt, 256 * nt);
-    k_radix_scatter<<<(unsigned)nt, 256, 0, st>>>(key[cur], perm[cur], key[cur ^ 1], perm[cur ^ 1], n,
-                                                  shift, hist + 256 * nt, nt);
+    scan_inclusive<int32_t>(src, hist + hn, hn, nullptr, scan_tmp, st, launches);
+    k_radix_excl<<<grid_for(hn, 256), 256, 0, st>>>(hist, hist + hn, hn);
+    k_radix_scatter<<<(unsigned)nt, 256, smem, st>>>(key[cur], perm[cur], key[cur ^ 1], perm[cur ^ 1], n, shift,
+                                                     bins, hist + hn, nt);
     *launches += 3;
     cur ^= 1;
   }

@@ -116,12 +116,15 @@ __global__ void k_square(const double* s, double* out, int k) {
 
 size_t jacobi_smem(int N) { return (2 * (size_t)N * N + N) * sizeof(double); }
 
+cudaError_t svd_set_attributes() {
+  return cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
 void jacobi_svd(const double* R, int64_t ldr, int N, double* W, double* V, double* sigma, double* Vout,
                 int* err, cudaStream_t st, int64_t* launches) {
   size_t smem = jacobi_smem(N);
   const int use_smem = smem <= 200 * 1024;
   if (!use_smem) smem = (size_t)N * sizeof(double);
-  cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_jacobi<<<1, kSvdThreads, smem, st>>>(R, ldr, N, W, V, sigma, Vout, use_smem, err);
   ++*launches;
 }

@@ -16,7 +16,8 @@
 //   n >  32: one thread block per tile in shared memory (k_tsqr_cta).
 // Both are persistent over the live tiles: the row counts are only known on the device.
 //
-// Precision: FP64 throughout, or (mixed) FP32 leaf tiles with FP64 tree and final QR.
+// Precision: FP64 throughout, or (mixed) FP32 leaf tiles and tree levels with the final QR
+// of the stacked block triangles in FP64.
 #include "tsqr_reg.cuh"
 
 namespace fig {
@@ -229,11 +230,17 @@ static void launch_cta(const TsqrBlock& b, const double* tri_in, double* tri_out
     smem = 64 * sizeof(E);
     gs = static_cast<E*>(scratch);
   }
-  cudaFuncSetAttribute(k_tsqr_cta<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int64_t blocks = tiles < 1 ? 1 : tiles;
   const int64_t cap = 152 * 2;
   if (blocks > cap) blocks = cap;
   k_tsqr_cta<E><<<(unsigned)blocks, kQrThreads, smem, st>>>(b, tri_in, tri_out, div_in, gs, few_only);
+}
+
+cudaError_t tsqr_set_attributes() {
+  cudaError_t e = cudaFuncSetAttribute(k_tsqr_cta<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tsqr_cta<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+  return e;
 }
 
 void tsqr_leaf(const TsqrBlock& b, bool mixed, cudaStream_t st, int64_t* launches) {
@@ -257,7 +264,9 @@ void tsqr_leaf(const TsqrBlock& b, bool mixed, cudaStream_t st, int64_t* launche
   ++*launches;
 }
 
-void tsqr_reduce(TsqrBlock& b, cudaStream_t st, int64_t* launches) {
+// Tree levels in float for the mixed path (the triangles stay stored in float64), in
+// float64 otherwise; the final QR of the stacked block triangles is always float64.
+void tsqr_reduce(TsqrBlock& b, bool mixed, cudaStream_t st, int64_t* launches) {
   void* scratch = b.scratch;
   int64_t div = b.tile;
   int64_t tiles = (b.bound + b.tile - 1) / b.tile;
@@ -265,11 +274,17 @@ void tsqr_reduce(TsqrBlock& b, cudaStream_t st, int64_t* launches) {
   for (int l = 0; l < b.levels; ++l) {
     const int64_t out_tiles = (tiles + b.fan - 1) / b.fan;
     if (b.nreg && b.nreg <= 16) {
-      launch_reg_n<double>(b, b.tri[cur], b.tri[cur ^ 1], div, out_tiles, st);
-      launch_cta<double>(b, b.tri[cur], b.tri[cur ^ 1], div, out_tiles, scratch, st, 1);
+      if (mixed) {
+        launch_reg_n<float>(b, b.tri[cur], b.tri[cur ^ 1], div, out_tiles, st);
+        launch_cta<float>(b, b.tri[cur], b.tri[cur ^ 1], div, out_tiles, scratch, st, 1);
+      } else {
+        launch_reg_n<double>(b, b.tri[cur], b.tri[cur ^ 1], div, out_tiles, st);
+        launch_cta<double>(b, b.tri[cur], b.tri[cur ^ 1], div, out_tiles, scratch, st, 1);
+      }
       *launches += 2;
     } else {
-      launch_cta<double>(b, b.tri[cur], b.tri[cur ^ 1], div, out_tiles, scratch, st);
+      if (mixed) launch_cta<float>(b, b.tri[cur], b.tri[cur ^ 1], div, out_tiles, scratch, st);
+      else launch_cta<double>(b, b.tri[cur], b.tri[cur ^ 1], div, out_tiles, scratch, st);
       ++*launches;
     }
     cur ^= 1;
@@ -284,7 +299,7 @@ void tsqr_final(const TsqrBlock* blocks_dev, int n_blocks, TsqrBlock& stack_blk,
   k_tsqr_stack<<<1, 256, 0, st>>>(blocks_dev, n_blocks, (int)stack_blk.M, N, const_cast<double*>(stack_blk.ptr));
   ++*launches;
   tsqr_leaf(stack_blk, false, st, launches);
-  tsqr_reduce(stack_blk, st, launches);
+  tsqr_reduce(stack_blk, false, st, launches);
   k_write_r<<<grid_for((int64_t)N * N, 256, 64), 256, 0, st>>>(stack_blk.tri[stack_blk.top], N, R, ldr);
   ++*launches;
 }
