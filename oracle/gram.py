@@ -66,14 +66,13 @@ def _aggregate(db, k):
         order, starts, uniq = rl.group_rows(kc)
         G = len(starts) - 1
         gid = np.empty(M, np.int64)
-        for g in range(G):
-            gid[order[starts[g]:starts[g + 1]]] = g
-        out_cnt = np.zeros(G)
-        np.add.at(out_cnt, gid, cnt)
+        gid[order] = np.repeat(np.arange(G), np.diff(starts))     # group of every row
+        out_cnt = np.bincount(gid, weights=cnt, minlength=G)
         out_sums = {}
         for l, s in sums.items():
             acc = np.zeros((G, s.shape[1]))
-            np.add.at(acc, gid, s)
+            for c in range(s.shape[1]):
+                acc[:, c] = np.bincount(gid, weights=s[:, c], minlength=G)
             out_sums[l] = acc
         return {"keys": uniq, "cnt": out_cnt, "sums": out_sums}
 

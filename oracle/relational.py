@@ -91,13 +91,26 @@ def group_rows(keys: np.ndarray):
     return order, starts, sk[head]
 
 
+def _row_ids(a: np.ndarray, b: np.ndarray):
+    """Number the distinct rows of the int64 matrices ``a`` and ``b`` (same width) jointly:
+    equal rows get equal ids.  Returns (ids of a's rows, ids of b's rows, number of ids)."""
+    both = np.concatenate([a, b], axis=0)
+    order, starts, _ = group_rows(both)
+    G = len(starts) - 1
+    ids = np.empty(both.shape[0], np.int64)
+    ids[order] = np.repeat(np.arange(G), np.diff(starts))
+    return ids[:a.shape[0]], ids[a.shape[0]:], G
+
+
 def match_rows(a: np.ndarray, b: np.ndarray) -> np.ndarray:
     """For every row of the int64 matrix ``a``, the index of the equal row of ``b`` (whose
     rows are distinct), or -1."""
     if a.shape[1] == 0:
         return np.zeros(a.shape[0], np.int64) if b.shape[0] == 1 else np.full(a.shape[0], -1)
-    lut = {tuple(r): i for i, r in enumerate(b.tolist())}
-    return np.array([lut.get(tuple(r), -1) for r in a.tolist()], dtype=np.int64)
+    ia, ib, u = _row_ids(a, b)
+    lut = np.full(u, -1, np.int64)
+    lut[ib] = np.arange(b.shape[0])
+    return lut[ia]
 
 
 # ---------------------------------------------------------------- natural join
@@ -160,8 +173,10 @@ def semijoin_keep(db_rel, other_rel, attrs):
     b = key_columns(other_rel, attrs)
     if len(attrs) == 0:
         return np.full(db_rel.n_rows, other_rel.n_rows > 0)
-    present = {tuple(r) for r in b.tolist()}
-    return np.array([tuple(r) in present for r in a.tolist()], dtype=bool)
+    ia, ib, u = _row_ids(a, b)
+    present = np.zeros(u, dtype=bool)
+    present[ib] = True
+    return present[ia]
 
 
 def full_reduce(db):

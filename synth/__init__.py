@@ -173,27 +173,31 @@ def snowflake(seed: int = 4, f_rows: int = 10_000_000, d1_rows: int = 1_000_000,
                     f"{n_scaled} cols x{scale:g}")
 
 
+def batch_instance(inst: int, seed: int = 5, lo: int = 1000, hi: int = 1_000_000,
+                   n_lo: int = 8, n_hi: int = 64, s: float = 1.1) -> Database:
+    """Instance ``inst`` of the batch of independent two-relation joins: log-uniform rows
+    per side in [lo, hi], Zipf(s) keys over ceil(max(m_S, m_T)/100) values with every key
+    present in both sides; n total data columns in U{n_lo..n_hi}, split floor(n/2) / rest.
+    Each instance has its own seeded generator, so instances can be drawn one at a time."""
+    rng = np.random.default_rng(seed * 100_003 + inst)
+    mS = int(np.exp(rng.uniform(np.log(lo), np.log(hi))))
+    mT = int(np.exp(rng.uniform(np.log(lo), np.log(hi))))
+    n = int(rng.integers(n_lo, n_hi + 1))
+    nS = n // 2
+    dom = max(1, -(-max(mS, mT) // 100))
+    dom = min(dom, mS, mT)
+    draw = lambda g, c: zipf_keys(g, c, dom, s)
+    kS = covering_keys(rng, mS, dom, draw)
+    kT = covering_keys(rng, mT, dom, draw)
+    S = Relation("S", (0,), kS[:, None], _normal(rng, mS, nS))
+    T = Relation("T", (0,), kT[:, None], _normal(rng, mT, n - nS))
+    return Database([S, T], [-1, 0], ["a"], f"batch instance {inst}")
+
+
 def batch_instances(seed: int = 5, count: int = 256, lo: int = 1000, hi: int = 1_000_000,
                     n_lo: int = 8, n_hi: int = 64, s: float = 1.1):
-    """Independent two-relation joins of uneven size (log-uniform rows per side),
-    Zipf(s) keys over ceil(max(m_S, m_T)/100) values with every key present in both
-    sides; n total data columns in U{n_lo..n_hi}, split floor(n/2) / rest."""
-    out = []
-    for inst in range(count):
-        rng = np.random.default_rng(seed * 100_003 + inst)
-        mS = int(np.exp(rng.uniform(np.log(lo), np.log(hi))))
-        mT = int(np.exp(rng.uniform(np.log(lo), np.log(hi))))
-        n = int(rng.integers(n_lo, n_hi + 1))
-        nS = n // 2
-        dom = max(1, -(-max(mS, mT) // 100))
-        dom = min(dom, mS, mT)
-        draw = lambda g, c: zipf_keys(g, c, dom, s)
-        kS = covering_keys(rng, mS, dom, draw)
-        kT = covering_keys(rng, mT, dom, draw)
-        S = Relation("S", (0,), kS[:, None], _normal(rng, mS, nS))
-        T = Relation("T", (0,), kT[:, None], _normal(rng, mT, n - nS))
-        out.append(Database([S, T], [-1, 0], ["a"], f"batch instance {inst}"))
-    return out
+    """The first ``count`` instances of the batch (see ``batch_instance``)."""
+    return [batch_instance(i, seed, lo, hi, n_lo, n_hi, s) for i in range(count)]
 
 
 def cartesian(seed: int = 6, m: int = 512, n: int = 64, m2: int = None, n2: int = None) -> Database:
