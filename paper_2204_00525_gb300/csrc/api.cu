@@ -59,6 +59,9 @@ struct Node {
   NodeBuf b{};
   int64_t n_tiles = 0;
   ChildLink link[kMaxChildren]{};      // one per child (filled for the parent's passes)
+  int32_t* radix_hist = nullptr;        // per relation: the sorts run concurrently
+  int32_t* radix_tmp = nullptr;
+  int blk_tails = -1, blk_gen = -1;     // R0 blocks fed by this relation (index into blocks)
 };
 
 }  // namespace fig
@@ -78,8 +81,6 @@ struct figaro_plan_s {
   int* err_host = nullptr;             // pinned: [0] error word, [4 + 4 i ..] sizes of node i
   double* beta = nullptr;
   int64_t beta_len = 0;
-  int32_t* radix_hist = nullptr;
-  int32_t* radix_scan_tmp = nullptr;
   std::vector<fig::TsqrBlock> blocks;
   fig::TsqrBlock* blocks_dev = nullptr;
   int stack_rows = 0;
@@ -87,6 +88,10 @@ struct figaro_plan_s {
   fig::TsqrBlock stack_blk{};          // the stacked block triangles (final QR)
   std::vector<cudaStream_t> side;      // one stream per R0 block: the TSQR chains run concurrently
   std::vector<cudaEvent_t> side_done;
+  std::vector<cudaStream_t> nstream;   // one stream per relation: sort, segmentation, heads/tails
+  cudaStream_t copy_st = nullptr;      // host-memory mode: input copies, keys first
+  std::vector<cudaEvent_t> ev_keys, ev_data, ev_seg, ev_leaf, ev_gen;
+  cudaEvent_t ev_counts = nullptr;
   cudaEvent_t fork = nullptr;
   cudaGraphExec_t graph_exec = nullptr;  // captured R pipeline (see run_r)
   cudaStream_t exec = nullptr;           // the plan's own stream: the graph runs here
@@ -138,13 +143,13 @@ static void layout(figaro_plan_s& P, Arena& a) {
   P.err_dev = a.take<int>(4);
   P.beta_len = std::min<int64_t>(maxM + 1, kBetaMax);
   P.beta = a.take<double>(P.beta_len);
-  const int64_t rh = radix_hist_elems(maxM);
-  P.radix_hist = a.take<int32_t>(2 * rh);
-  P.radix_scan_tmp = a.take<int32_t>(scan_tmp_elems(rh));
   for (auto& n : P.nodes) {
     NodeBuf& b = n.b;
     const int64_t M = n.M;
     const int nch = (int)n.children.size();
+    const int64_t rh = radix_hist_elems(M);
+    n.radix_hist = a.take<int32_t>(2 * rh);
+    n.radix_tmp = a.take<int32_t>(scan_tmp_elems(rh));
     if (P.opt.mem == FIGARO_MEM_HOST) {
       for (int k = 0; k < n.K; ++k)
         n.dkey[k] = n.key_type == FIGARO_KEY_I32 ? (void*)a.take<int32_t>(M) : (void*)a.take<int64_t>(M);
@@ -459,7 +464,9 @@ static void make_blocks(figaro_plan_s& P) {
   P.blocks.clear();
   P.stack_rows = 0;
   for (auto& n : P.nodes) {
+    n.blk_tails = n.blk_gen = -1;
     if (n.N > 0) {
+      n.blk_tails = (int)P.blocks.size();
       TsqrBlock t{};
       t.n = n.N;
       t.kind = BLK_TAILS;
@@ -470,6 +477,7 @@ static void make_blocks(figaro_plan_s& P) {
       P.stack_rows += t.n;
     }
     if (!n.leaf && !n.root && n.N_sub > 0) {
+      n.blk_gen = (int)P.blocks.size();
       TsqrBlock t{};
       t.n = n.N_sub;
       t.kind = BLK_GEN;
@@ -480,6 +488,7 @@ static void make_blocks(figaro_plan_s& P) {
       P.stack_rows += t.n;
     }
     if (n.root) {
+      n.blk_gen = (int)P.blocks.size();
       TsqrBlock t{};
       t.n = n.N_sub;
       t.kind = BLK_ROOT;
@@ -561,44 +570,87 @@ struct StageClock {
   }
 };
 
+// The pipeline as a dependency graph over streams:
+//   copies (host-memory mode)  keys of every relation, then the data in post-order
+//   relation i                 pack + sort + segmentation       (needs its keys)
+//   main                       Alg. 3 counts                      (needs every segmentation)
+//   relation i                 heads and tails                    (needs counts and its data)
+//   block stream               TSQR of relation i's tails block   (needs its heads and tails)
+//   main                       join + project-away, post-order    (needs the heads of the node
+//                                                                  and of its leaf children)
+//   block stream               TSQR of each generalized-tail / root block (after its join)
+//   main                       final QR of the stacked triangles  (needs every block)
+// With stage timing everything runs in that order on the main stream instead, the TSQR
+// chains last, so that each stage's event times cover only its own kernels.
 static int enqueue_r(figaro_plan_s& P, double* R, int64_t ldr) {
   cudaStream_t st = P.st;
   const bool mixed = P.opt.precision == FIGARO_PREC_MIXED;
+  const bool serial = P.opt.stage_timing != 0;
+  const bool host = P.opt.mem == FIGARO_MEM_HOST;
+  const int r = (int)P.nodes.size();
   P.launches = 0;
+  auto nst = [&](int i) { return serial ? st : P.nstream[i]; };
+  auto rec = [&](cudaEvent_t e, cudaStream_t s) { return serial ? cudaSuccess : cudaEventRecord(e, s); };
+  auto wait = [&](cudaStream_t s, cudaEvent_t e) { return serial ? cudaSuccess : cudaStreamWaitEvent(s, e, 0); };
   FIG_CUDA(cudaMemsetAsync(P.err_dev, 0, sizeof(int), st));
-  if (P.opt.mem == FIGARO_MEM_HOST) {
-    for (auto& n : P.nodes) {
+  FIG_CUDA(rec(P.fork, st));
+  if (host) {
+    cudaStream_t cs = serial ? st : P.copy_st;
+    FIG_CUDA(wait(cs, P.fork));
+    for (int i = 0; i < r; ++i) {
+      Node& n = P.nodes[i];
       for (int k = 0; k < n.K; ++k)
         FIG_CUDA(cudaMemcpyAsync(n.dkey[k], n.key_ptr[k], n.M * (n.key_type == FIGARO_KEY_I32 ? 4 : 8),
-                                 cudaMemcpyHostToDevice, st));
+                                 cudaMemcpyHostToDevice, cs));
+      FIG_CUDA(rec(P.ev_keys[i], cs));
+    }
+    for (int i : P.post) {
+      Node& n = P.nodes[i];
       if (n.N > 0) {
         const int64_t elems = n.layout == FIGARO_COL_MAJOR ? n.ld * (n.N - 1) + n.M : n.ld * (n.M - 1) + n.N;
-        FIG_CUDA(cudaMemcpyAsync(n.ddata, n.data, elems * sizeof(double), cudaMemcpyHostToDevice, st));
+        FIG_CUDA(cudaMemcpyAsync(n.ddata, n.data, elems * sizeof(double), cudaMemcpyHostToDevice, cs));
       }
+      FIG_CUDA(rec(P.ev_data[i], cs));
     }
   }
+  // TSQR of one R0 block: on its own stream after `ready`, or in place when serial
+  auto run_block = [&](int bi, cudaEvent_t ready) -> int {
+    cudaStream_t s = serial ? st : P.side[bi];
+    FIG_CUDA(wait(s, ready));
+    if (serial) FIG_CUDA(cudaEventRecord(P.leaf_ev[2 * bi], s));
+    const int64_t l0 = P.launches;
+    tsqr_leaf(P.blocks[bi], mixed, s, &P.launches);
+    P.stage_launch[5] += P.launches - l0;
+    if (serial) FIG_CUDA(cudaEventRecord(P.leaf_ev[2 * bi + 1], s));
+    tsqr_reduce(P.blocks[bi], mixed, s, &P.launches);
+    FIG_CUDA(rec(P.side_done[bi], s));
+    return FIGARO_OK;
+  };
   StageClock clk(P);
   // ---- stage 0: pack + sort
   clk.start(0);
-  for (auto& n : P.nodes) {
+  for (int i = 0; i < r; ++i) {
+    Node& n = P.nodes[i];
+    cudaStream_t s = nst(i);
+    FIG_CUDA(wait(s, host ? P.ev_keys[i] : P.fork));
     PackParams pp{};
     pp.n_keys = (int)n.pack_attr.size();
     pp.key_type = n.key_type;
     for (int k = 0; k < pp.n_keys; ++k) {
       const int col = n.pack_col[k];
-      pp.cols[k] = P.opt.mem == FIGARO_MEM_HOST ? n.dkey[col] : n.key_ptr[col];
+      pp.cols[k] = host ? n.dkey[col] : n.key_ptr[col];
       pp.kmin[k] = P.amin[n.pack_attr[k]];
       pp.shift[k] = n.shift[k];
       pp.bits[k] = P.abits[n.pack_attr[k]];
     }
     const bool sort = !P.opt.presorted && n.bits > 0;
-    launch_pack(pp, n.M, n.b.key[0], sort ? n.b.perm[0] : nullptr, P.err_dev, st, &P.launches);
+    launch_pack(pp, n.M, n.b.key[0], sort ? n.b.perm[0] : nullptr, P.err_dev, s, &P.launches);
     if (sort) {
-      int cur = radix_sort(n.b.key, n.b.perm, n.M, n.bits, P.radix_hist, P.radix_scan_tmp, st, &P.launches);
+      int cur = radix_sort(n.b.key, n.b.perm, n.M, n.bits, n.radix_hist, n.radix_tmp, s, &P.launches);
       n.b.skey = n.b.key[cur];
       n.b.sperm = n.b.perm[cur];
     } else {
-      if (P.opt.presorted) check_sorted(n.b.key[0], n.M, P.err_dev, st, &P.launches);
+      if (P.opt.presorted) check_sorted(n.b.key[0], n.M, P.err_dev, s, &P.launches);
       n.b.skey = n.b.key[0];
       n.b.sperm = nullptr;
     }
@@ -606,7 +658,11 @@ static int enqueue_r(figaro_plan_s& P, double* R, int64_t ldr) {
   clk.stop();
   // ---- stage 1: segmentation
   clk.start(1);
-  for (auto& n : P.nodes) segment(n.b, n.M, n.rest_bits, st, &P.launches);
+  for (int i = 0; i < r; ++i) {
+    segment(P.nodes[i].b, P.nodes[i].M, P.nodes[i].rest_bits, nst(i), &P.launches);
+    FIG_CUDA(rec(P.ev_seg[i], nst(i)));
+    FIG_CUDA(wait(st, P.ev_seg[i]));
+  }
   clk.stop();
   // ---- stage 2: counts (Alg. 3)
   clk.start(2);
@@ -655,14 +711,19 @@ static int enqueue_r(figaro_plan_s& P, double* R, int64_t ldr) {
     }
     join_prep(count_params(n), st, &P.launches);
   }
+  FIG_CUDA(rec(P.ev_counts, st));
   clk.stop();
-  // ---- stage 3: heads and tails of every relation
+  // ---- stage 3: heads and tails of every relation; each tails block's TSQR follows at once
   clk.start(3);
-  for (auto& n : P.nodes) {
+  for (int i = 0; i < r; ++i) {
+    Node& n = P.nodes[i];
+    cudaStream_t s = nst(i);
+    FIG_CUDA(wait(s, P.ev_counts));
+    if (host) FIG_CUDA(wait(s, P.ev_data[i]));
     LeafParams lp{};
     lp.M = n.M;
     lp.N = n.N;
-    lp.data = P.opt.mem == FIGARO_MEM_HOST ? n.ddata : n.data;
+    lp.data = host ? n.ddata : n.data;
     lp.rs = n.layout == FIGARO_COL_MAJOR ? 1 : n.ld;
     lp.cs = n.layout == FIGARO_COL_MAJOR ? n.ld : 1;
     lp.perm = n.b.sperm;
@@ -683,7 +744,12 @@ static int enqueue_r(figaro_plan_s& P, double* R, int64_t ldr) {
     lp.lflag = n.b.lflag;
     lp.lsum = n.b.lsum;
     lp.n_tiles = n.n_tiles;
-    leaf_heads_tails(lp, st, &P.launches);
+    leaf_heads_tails(lp, s, &P.launches);
+    FIG_CUDA(rec(P.ev_leaf[i], s));
+    if (!serial && n.blk_tails >= 0) {
+      const int rc = run_block(n.blk_tails, P.ev_leaf[i]);
+      if (rc != FIGARO_OK) return rc;
+    }
   }
   clk.stop();
   // ---- stage 4: join children, project away, root rows (post-order)
@@ -691,6 +757,8 @@ static int enqueue_r(figaro_plan_s& P, double* R, int64_t ldr) {
   for (int i : P.post) {
     Node& n = P.nodes[i];
     if (n.leaf && !n.root) continue;
+    FIG_CUDA(wait(st, P.ev_leaf[i]));
+    for (int c : n.children) FIG_CUDA(wait(st, P.ev_leaf[c]));
     GenParams gp{};
     gp.N = n.N_sub;
     gp.n_child = (int)n.children.size();
@@ -720,26 +788,22 @@ static int enqueue_r(figaro_plan_s& P, double* R, int64_t ldr) {
     gp.n_tiles = n.n_tiles;
     gp.is_root = n.root;
     if (gp.N > 0) gen_heads_tails(gp, st, &P.launches);
+    FIG_CUDA(rec(P.ev_gen[i], st));
+    if (!serial && n.blk_gen >= 0) {
+      const int rc = run_block(n.blk_gen, P.ev_gen[i]);
+      if (rc != FIGARO_OK) return rc;
+    }
   }
   clk.stop();
-  // ---- stages 5-6: TSQR of every R0 block, each on its own stream (the blocks are
-  // independent), then the final QR of their stacked triangles on the main stream.
-  // With stage timing the chains run one after another on the main stream instead, so
-  // that the leaf kernels' event times are not shared with concurrent work: stage 5 sums
-  // the leaf launches, stage 6 is the wall time of the whole TSQR section.
+  // ---- stages 5-6: with stage timing the TSQR chains run here, one after another (stage 5
+  // sums the leaf launches, stage 6 is the wall time of the whole TSQR section); then the
+  // final QR of the stacked block triangles on the main stream.
   clk.start(6);
-  FIG_CUDA(cudaEventRecord(P.fork, st));
   for (size_t bi = 0; bi < P.blocks.size(); ++bi) {
-    cudaStream_t s = P.opt.stage_timing ? st : P.side[bi];
-    if (!P.opt.stage_timing) FIG_CUDA(cudaStreamWaitEvent(s, P.fork, 0));
-    if (P.opt.stage_timing) FIG_CUDA(cudaEventRecord(P.leaf_ev[2 * bi], s));
-    const int64_t l0 = P.launches;
-    tsqr_leaf(P.blocks[bi], mixed, s, &P.launches);
-    P.stage_launch[5] += P.launches - l0;
-    if (P.opt.stage_timing) FIG_CUDA(cudaEventRecord(P.leaf_ev[2 * bi + 1], s));
-    tsqr_reduce(P.blocks[bi], mixed, s, &P.launches);
-    if (!P.opt.stage_timing) {
-      FIG_CUDA(cudaEventRecord(P.side_done[bi], s));
+    if (serial) {
+      const int rc = run_block((int)bi, nullptr);
+      if (rc != FIGARO_OK) return rc;
+    } else {
       FIG_CUDA(cudaStreamWaitEvent(st, P.side_done[bi], 0));
     }
   }
@@ -872,6 +936,13 @@ int figaro_plan_destroy(figaro_plan_t p) {
   if (p->exec) cudaStreamDestroy(p->exec);
   for (auto& s : p->side)
     if (s) cudaStreamDestroy(s);
+  for (auto& s : p->nstream)
+    if (s) cudaStreamDestroy(s);
+  if (p->copy_st) cudaStreamDestroy(p->copy_st);
+  for (auto* v : {&p->ev_keys, &p->ev_data, &p->ev_seg, &p->ev_leaf, &p->ev_gen})
+    for (auto& e : *v)
+      if (e) cudaEventDestroy(e);
+  if (p->ev_counts) cudaEventDestroy(p->ev_counts);
   if (p->err_host) cudaFreeHost(p->err_host);
   if (p->arena) cudaFree(p->arena);
   delete p;
@@ -940,15 +1011,31 @@ int figaro_plan(const figaro_join_tree* tree, const figaro_options* opt, void* s
   e = cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->join_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->join_out, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->exec, cudaStreamNonBlocking);
   if (e != cudaSuccess) return bail(e, "cudaEventCreate");
+  // the TSQR block streams get the lowest priority: their persistent kernels yield SMs to
+  // the relation and main streams, which carry the longer dependency chain
+  int prio_lo = 0, prio_hi = 0;
+  e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&P->exec, cudaStreamNonBlocking, prio_hi);
+  if (e != cudaSuccess) return bail(e, "plan streams");
   P->side.assign(P->blocks.size(), nullptr);
   P->side_done.assign(P->blocks.size(), nullptr);
   for (size_t bi = 0; bi < P->blocks.size(); ++bi) {
-    e = cudaStreamCreateWithFlags(&P->side[bi], cudaStreamNonBlocking);
+    e = cudaStreamCreateWithPriority(&P->side[bi], cudaStreamNonBlocking, prio_lo);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->side_done[bi], cudaEventDisableTiming);
     if (e != cudaSuccess) return bail(e, "side streams");
   }
+  const size_t r = P->nodes.size();
+  P->nstream.assign(r, nullptr);
+  for (auto* v : {&P->ev_keys, &P->ev_data, &P->ev_seg, &P->ev_leaf, &P->ev_gen}) v->assign(r, nullptr);
+  for (size_t i = 0; i < r && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithPriority(&P->nstream[i], cudaStreamNonBlocking, prio_hi);
+    for (auto* v : {&P->ev_keys, &P->ev_data, &P->ev_seg, &P->ev_leaf, &P->ev_gen})
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&(*v)[i], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&P->copy_st, cudaStreamNonBlocking, prio_hi);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->ev_counts, cudaEventDisableTiming);
+  if (e != cudaSuccess) return bail(e, "relation streams");
   P->leaf_ev.assign(2 * P->blocks.size(), nullptr);
   for (auto& ev : P->leaf_ev) {
     e = cudaEventCreate(&ev);

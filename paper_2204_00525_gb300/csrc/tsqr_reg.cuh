@@ -206,9 +206,18 @@ __global__ void __launch_bounds__(128) k_tsqr_reg(TsqrBlock b, const double* tri
 template <typename E, int N>
 void launch_reg(const TsqrBlock& b, const double* tri_in, double* tri_out, int64_t div_in, int64_t tiles,
                 cudaStream_t st) {
+  // persistent: as many 4-warp blocks as are resident at once (registers decide), so that
+  // no second, partial wave of blocks runs at low occupancy
+  static int resident = 0;
+  if (resident == 0) {
+    int per_sm = 0, sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tsqr_reg<E, N>, 128, 0);
+    resident = (per_sm > 0 && sms > 0) ? per_sm * sms : 152 * 4;
+  }
   int64_t blocks = (tiles + 3) / 4;
-  const int64_t cap = 152 * 4;               // persistent: up to 4 blocks of 4 warps per SM
-  if (blocks > cap) blocks = cap;
+  if (blocks > resident) blocks = resident;
   if (blocks < 1) blocks = 1;
   k_tsqr_reg<E, N><<<(unsigned)blocks, 128, 0, st>>>(b, tri_in, tri_out, div_in);
 }
