@@ -139,6 +139,23 @@ def time_steps(plan, torch, steps, warmup, barrier):
     return e0.elapsed_time(e1) / steps
 
 
+def run_plan_only(args):
+    """--plan-only: W + K calls of one plan on the benchmark workload and nothing else
+    (no JSON line): a short, deterministic launch sequence for ncu captures."""
+    import torch
+    from paper_2204_00525_gb300 import binding
+    binding.load(build_if_missing=True)
+    db = synth.path3(seed=2, rows=args.rows)
+    dev_inputs = make_inputs(db, torch, "cuda")
+    prec = binding.FIGARO_PREC_MIXED if args.plan_only.startswith("mixed") else binding.FIGARO_PREC_FP64
+    p = binding.JoinPlan(dev_inputs, db.parent, precision=prec, stage_timing=args.plan_only.endswith("staged"),
+                         stream=torch.cuda.current_stream())
+    p._R = torch.empty(db.n_cols, db.n_cols, dtype=torch.float64, device="cuda")
+    ms = time_steps(p, torch, args.steps, args.warmup, lambda: None)
+    p.close()
+    log(f"{args.plan_only}: {ms:.3f} ms per step")
+
+
 def run_figaro(args):
     import torch
     from paper_2204_00525_gb300 import binding
@@ -316,10 +333,14 @@ def main():
     ap.add_argument("--rows", type=int, default=ROWS)
     ap.add_argument("--sample-rows", type=int, default=SAMPLE_ROWS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plan-only", choices=["fp64", "mixed", "fp64-staged", "mixed-staged"],
+                    help="profiling aid: run one plan only and print no JSON line")
     args = ap.parse_args()
     if args.warmup < 3:
         log("warning: fewer than 3 warm-up steps")
-    if args.impl == "reference":
+    if args.plan_only:
+        run_plan_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_figaro(args)

@@ -173,6 +173,7 @@ static void layout(figaro_plan_s& P, Arena& a) {
     b.full = a.take<uint64_t>(M);
     b.phic = a.take<uint64_t>(M);
     b.phid = a.take<uint64_t>(M);
+    b.sq_phid = a.take<double>(M);
     b.phiu = a.take<uint64_t>(M);
     b.theta_incl = a.take<uint64_t>(M);
     b.sq_phic = a.take<double>(M);
@@ -181,6 +182,8 @@ static void layout(figaro_plan_s& P, Arena& a) {
     b.fac = a.take<double>(M * (1 + nch));
     b.vw = a.take<double>(3 * M);
     b.hf = a.take<double>(M);
+    b.lds = (M + 7) & ~int64_t(7);
+    b.sdata = a.take<double>(b.lds * std::max(n.N, 1));
     b.heads = a.take<double>(M * std::max(n.N, 1));
     b.tails = a.take<double>(M * std::max(n.N, 1));
     b.tails32 = mixed ? a.take<float>(M * std::max(n.N, 1)) : nullptr;
@@ -451,6 +454,7 @@ static void make_links(figaro_plan_s& P) {
       L.pkey = c.b.pkey;
       L.sizes = c.b.sizes;
       L.phid = c.b.phid;
+      L.sq_phid = c.b.sq_phid;
       L.phiu = c.b.phiu;
       L.q = n.b.q + (int64_t)jj * n.M;
       L.data = c.leaf ? c.b.heads : c.b.data2;
@@ -660,6 +664,7 @@ static int enqueue_r(figaro_plan_s& P, double* R, int64_t ldr) {
   clk.start(1);
   for (int i = 0; i < r; ++i) {
     segment(P.nodes[i].b, P.nodes[i].M, P.nodes[i].rest_bits, nst(i), &P.launches);
+    counts_clear(P.nodes[i].b, P.nodes[i].M, nst(i), &P.launches);
     FIG_CUDA(rec(P.ev_seg[i], nst(i)));
     FIG_CUDA(wait(st, P.ev_seg[i]));
   }
@@ -692,10 +697,6 @@ static int enqueue_r(figaro_plan_s& P, double* R, int64_t ldr) {
     c.hf = n.b.hf;
     return c;
   };
-  for (auto& n : P.nodes) {
-    FIG_CUDA(cudaMemsetAsync(n.b.phid, 0, sizeof(uint64_t) * n.M, st));
-    FIG_CUDA(cudaMemsetAsync(n.b.phiu, 0, sizeof(uint64_t) * n.M, st));
-  }
   for (int i : P.post) counts_pass1(count_params(P.nodes[i]), st, P.err_dev, &P.launches);
   for (int i : P.pre) {
     Node& n = P.nodes[i];
@@ -727,6 +728,8 @@ static int enqueue_r(figaro_plan_s& P, double* R, int64_t ldr) {
     lp.rs = n.layout == FIGARO_COL_MAJOR ? 1 : n.ld;
     lp.cs = n.layout == FIGARO_COL_MAJOR ? n.ld : 1;
     lp.perm = n.b.sperm;
+    lp.sdata = n.b.sperm ? n.b.sdata : nullptr;
+    lp.lds = n.b.lds;
     lp.row_gid = n.b.row_gid;
     lp.goff = n.b.goff;
     lp.sq_phic = n.b.sq_phic;

@@ -95,5 +95,8 @@ struct ScanSrc {
 template <typename T>
 void scan_inclusive(const ScanSrc& src, T* out, int64_t n_max, const int32_t* n_dev, T* tmp,
                     cudaStream_t st, int64_t* launches);
+// Exclusive prefix sums of n_max int32 elements (all live).
+void scan_exclusive_i32(const ScanSrc& src, int32_t* out, int64_t n_max, int32_t* tmp, cudaStream_t st,
+                        int64_t* launches);
 
 }  // namespace fig

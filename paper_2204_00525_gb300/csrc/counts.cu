@@ -3,6 +3,8 @@
 // pass 1 (post-order over the join tree), one thread per group x_i of S_i:
 //   rows_per_key(x_i) = group size, Theta_down(x_i) = rows * prod_children Phi_down_j(x_ij),
 //   Phi_down_i(x_p) += Theta_down(x_i)   (integer atomics: order-independent, exact).
+// The atomics are combined per warp first (one atomic per distinct target and warp): with
+// Zipf-skewed keys thousands of groups add into the same few x_p.
 // pass 2 (pre-order):
 //   full_join_size(x_i) = Theta_down(x_i) * Phi_up_i(x_p)  (1 at the root),
 //   Phi_up_j(x_ij) += full_join_size(x_i) for every child j,
@@ -33,47 +35,84 @@ __device__ __forceinline__ uint64_t project_key(const ChildLink& c, uint64_t key
   return x;
 }
 
+// arr[idx] += v for every lane with `on`; all 32 lanes of the warp must call it.  Lanes
+// with equal idx are summed first (checked for overflow), and their lowest lane adds.
+__device__ __forceinline__ void warp_combined_add(uint64_t* arr, int32_t idx, uint64_t v, bool on, int* err) {
+  const int lane = threadIdx.x & 31;
+  const unsigned peers = __match_any_sync(0xffffffffu, on ? idx : -1 - lane);
+  uint64_t sum = 0;
+  bool wrap = false;
+#pragma unroll
+  for (int t = 0; t < 32; ++t) {
+    const uint64_t o = __shfl_sync(0xffffffffu, v, t);
+    if ((peers >> t) & 1u) {
+      wrap |= sum + o < sum;
+      sum += o;
+    }
+  }
+  if (on && lane == __ffs(peers) - 1 && sum) {
+    const unsigned long long old = atomicAdd((unsigned long long*)&arr[idx], (unsigned long long)sum);
+    if (wrap || old + sum < old) set_error(err, FIGARO_ERR_OVERFLOW);
+  }
+}
+
+// Zeroes Phi_down and Phi_up over the P parent groups of a relation.
+__global__ void k_counts_clear(uint64_t* phid, uint64_t* phiu, const int32_t* sizes) {
+  const int64_t P = sizes[1];
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < P; q += (int64_t)gridDim.x * blockDim.x) {
+    phid[q] = 0ull;
+    phiu[q] = 0ull;
+  }
+}
+
+// Grid-stride loops below keep whole warps together (g - lane is warp-uniform) so that
+// the warp-combined atomics see all 32 lanes.
 __global__ void k_counts_pass1(CountParams p, int* err) {
   const int64_t G = p.sizes[0];
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < G;
+  const int lane = threadIdx.x & 31;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g - lane < G;
        g += (int64_t)gridDim.x * blockDim.x) {
-    uint64_t rows = (uint64_t)(p.goff[g + 1] - p.goff[g]);
-    uint64_t theta = rows;
-    for (int j = 0; j < p.n_child; ++j) {
-      const ChildLink& c = p.ch[j];
-      int32_t q = find_key(c.pkey, c.sizes[1], project_key(c, p.gkey[g]));
-      c.q[g] = q;
-      theta = q < 0 ? 0ull : mul_chk(theta, c.phid[q], err);
+    const bool on = g < G;
+    uint64_t theta = 0;
+    int32_t pg = 0;
+    if (on) {
+      theta = (uint64_t)(p.goff[g + 1] - p.goff[g]);
+      for (int j = 0; j < p.n_child; ++j) {
+        const ChildLink& c = p.ch[j];
+        int32_t q = find_key(c.pkey, c.sizes[1], project_key(c, p.gkey[g]));
+        c.q[g] = q;
+        theta = q < 0 ? 0ull : mul_chk(theta, c.phid[q], err);
+      }
+      p.theta[g] = theta;
+      pg = p.is_root ? 0 : p.g2p[g];
     }
-    p.theta[g] = theta;
-    if (!p.is_root && theta) {
-      unsigned long long old = atomicAdd((unsigned long long*)&p.phid[p.g2p[g]], (unsigned long long)theta);
-      if (old + theta < old) set_error(err, FIGARO_ERR_OVERFLOW);
-    }
+    if (!p.is_root) warp_combined_add(p.phid, pg, theta, on && theta, err);
   }
 }
 
 __global__ void k_counts_pass2(CountParams p, int* err) {
   const int64_t G = p.sizes[0];
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < G;
+  const int lane = threadIdx.x & 31;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g - lane < G;
        g += (int64_t)gridDim.x * blockDim.x) {
-    uint64_t rows = (uint64_t)(p.goff[g + 1] - p.goff[g]);
-    uint64_t up = p.is_root ? 1ull : p.phiu[p.g2p[g]];
-    uint64_t full = mul_chk(p.theta[g], up, err);
-    p.full[g] = full;
+    const bool on = g < G;
+    uint64_t full = 0;
+    if (on) {
+      const uint64_t rows = (uint64_t)(p.goff[g + 1] - p.goff[g]);
+      const uint64_t up = p.is_root ? 1ull : p.phiu[p.g2p[g]];
+      full = mul_chk(p.theta[g], up, err);
+      p.full[g] = full;
+      const uint64_t circ = full / rows;
+      p.phic[g] = circ;
+      if (p.require_reduced && circ == 0) set_error(err, FIGARO_ERR_NOT_REDUCED);
+      p.sq_phic[g] = sqrt((double)circ);
+      p.hrow[g] = 1.0 / sqrt((double)rows);
+    }
     for (int j = 0; j < p.n_child; ++j) {
       const ChildLink& c = p.ch[j];
-      int32_t q = c.q[g];
-      if (q >= 0 && full) {
-        unsigned long long old = atomicAdd((unsigned long long*)&c.phiu[q], (unsigned long long)full);
-        if (old + full < old) set_error(err, FIGARO_ERR_OVERFLOW);
-      }
+      const int32_t q = on ? c.q[g] : -1;
+      warp_combined_add(c.phiu, q, full, q >= 0 && full, err);
     }
-    uint64_t circ = full / rows;
-    p.phic[g] = circ;
-    if (p.require_reduced && circ == 0) set_error(err, FIGARO_ERR_NOT_REDUCED);
-    p.sq_phic[g] = sqrt((double)circ);
-    p.hrow[g] = 1.0 / sqrt((double)rows);
   }
 }
 
@@ -83,6 +122,7 @@ __global__ void k_counts_finalize(ChildLink c) {
        q += (int64_t)gridDim.x * blockDim.x) {
     uint64_t d = c.phid[q];
     c.phiu[q] = d ? c.phiu[q] / d : 0ull;
+    c.sq_phid[q] = sqrt((double)d);
   }
 }
 
@@ -105,11 +145,11 @@ __global__ void k_join_prep(CountParams p) {
     double all = 1.0;
     for (int j = 0; j < p.n_child; ++j) {
       int32_t q = p.ch[j].q[g];
-      s[j] = q >= 0 ? sqrt((double)p.ch[j].phid[q]) : 0.0;
+      s[j] = q >= 0 ? p.ch[j].sq_phid[q] : 0.0;
       all *= s[j];
     }
     const uint64_t rows = (uint64_t)(p.goff[g + 1] - p.goff[g]);
-    const double sr = sqrt((double)rows);
+    const double sr = (double)rows * p.hrow[g];        // sqrt(rows) = rows / sqrt(rows)
     p.fac[g * nf] = all;
     for (int j = 0; j < p.n_child; ++j) {
       double o = sr;
@@ -138,6 +178,11 @@ __global__ void k_join_prep(CountParams p) {
     p.vw[g * 3 + 1] = W;
     p.vw[g * 3 + 2] = gam;
   }
+}
+
+void counts_clear(NodeBuf& b, int64_t bound, cudaStream_t st, int64_t* launches) {
+  k_counts_clear<<<grid_for(bound, 256, 152 * 4), 256, 0, st>>>(b.phid, b.phiu, b.sizes);
+  ++*launches;
 }
 
 void counts_pass1(const CountParams& p, cudaStream_t st, int* err, int64_t* launches) {

@@ -1,5 +1,5 @@
 // Double-float arithmetic on the FP32 pipe: a value is an unevaluated sum hi + lo of two
-// floats (about 48 significant bits).  Used by the mixed-precision head/tail scans, which
+// floats (about 47 significant bits).  Used by the mixed-precision head/tail scans, which
 // must keep their prefix sums accurate without paying for FP64 instructions (GB300 runs
 // FP64 at 1/64 of the FP32 rate).
 //
@@ -50,17 +50,31 @@ __device__ __forceinline__ dfl df_mul_f(dfl a, float b) {
   return r;
 }
 
-// Exact split of a non-negative integer below 2^48 into hi + lo floats.
-__device__ __forceinline__ dfl df_from_count(int64_t p) {
-  const float h = (float)p;                       // rounds to 24 bits
-  const float l = (float)(p - (int64_t)h);        // remainder below 2^24 in magnitude: exact
-  return dfl{h, l};
+// Integer -> float without conversion instructions (64-bit conversions run on the FP64
+// pipe of this part): a float of exponent 2^23 holds an integer below 2^23 in its
+// mantissa, so or-ing the integer in and subtracting 2^23 is exact.
+__device__ __forceinline__ float small_u23_to_float(uint32_t v) {     // v < 2^23
+  return __uint_as_float(0x4B000000u | v) - 8388608.0f;
 }
 
-// Split a double x into hi + lo with |x - hi - lo| <= 2^-46 |x| without FP64
-// instructions: hi takes the sign, the exponent and the leading 23 bits of the
-// mantissa (truncated), lo the remaining 29 bits rounded to a float and scaled by
-// 2^(e - 1075).  Outside |x| in [2^-74, 2^127] (zero, tiny or huge values) the FP64
+// Exact split of a non-negative integer below 2^31 into hi + lo floats: the high 15 bits
+// scaled by 2^16 plus the low 16 bits, renormalised by Fast2Sum (both exact in float).
+__device__ __forceinline__ dfl df_from_count(int32_t p) {
+  const uint32_t u = (uint32_t)p;
+  const float h = small_u23_to_float(u >> 16) * 65536.0f;
+  const float l = small_u23_to_float(u & 0xFFFFu);
+  dfl r;
+  fast_two(h, l, r.hi, r.lo);
+  return r;
+}
+
+// Split a double x into hi + lo with |x - hi - lo| <= 2^-47 |x| without FP64 or
+// conversion instructions: hi takes the sign, the exponent and the leading 23 bits of
+// the mantissa (truncated); lo is the remaining 29-bit integer u, rounded to a multiple of
+// 64 (|error| <= 32), times 2^(e - 1075).  The rounding uses a float of exponent 2^29,
+// whose mantissa steps are 64: adding (u + 32) / 64 to its bit pattern gives 2^29 + 64 k
+// (a carry into the exponent gives 2^30 = 2^29 + 64 * 2^23), and subtracting 2^29 is
+// exact (Sterbenz).  Outside |x| in [2^-74, 2^127] (zero, tiny or huge values) the FP64
 // conversion is used instead.
 __device__ __forceinline__ dfl df_from_double(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
@@ -74,7 +88,9 @@ __device__ __forceinline__ dfl df_from_double(double x) {
   const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
   const float h = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)(m >> 29));
   const float scale = __uint_as_float((unsigned)(e - 1075 + 127) << 23);   // 2^(e - 1075)
-  float l = (float)(unsigned)(m & 0x1FFFFFFFull) * scale;
+  const uint32_t u = (uint32_t)(m & 0x1FFFFFFFull);
+  const float k64 = __uint_as_float((156u << 23) + ((u + 32u) >> 6)) - 536870912.0f;
+  float l = k64 * scale;
   if (sign) l = -l;
   return dfl{h, l};
 }

@@ -125,6 +125,41 @@ __device__ __forceinline__ LeafRow leaf_row(const LeafParams& p, int64_t e) {
   return r;
 }
 
+// The kHtItems values of column c for one lane's consecutive sorted rows: gathered through
+// the permutation (first pass; a copy in sorted order is kept when p.sdata is set), or read
+// back from that copy (last pass) with 16-byte loads.
+__device__ __forceinline__ void load_leaf_items(const LeafParams& p, const LeafRow (&rw)[kHtItems], int64_t e0,
+                                                int c, bool from_copy, double (&xs)[kHtItems]) {
+  if (from_copy) {
+    const double* col = p.sdata + (int64_t)c * p.lds + e0;
+    if (e0 + kHtItems <= p.M) {
+#pragma unroll
+      for (int i = 0; i < kHtItems; i += 2) {
+        const double2 v = *reinterpret_cast<const double2*>(col + i);
+        xs[i] = v.x;
+        xs[i + 1] = v.y;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < kHtItems; ++i) xs[i] = rw[i].ok ? col[i] : 0.0;
+    }
+    return;
+  }
+#pragma unroll
+  for (int i = 0; i < kHtItems; ++i) xs[i] = rw[i].ok ? p.data[(int64_t)rw[i].src * p.rs + (int64_t)c * p.cs] : 0.0;
+  if (p.sdata) {
+    double* col = p.sdata + (int64_t)c * p.lds + e0;
+    if (e0 + kHtItems <= p.M) {
+#pragma unroll
+      for (int i = 0; i < kHtItems; i += 2) *reinterpret_cast<double2*>(col + i) = make_double2(xs[i], xs[i + 1]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < kHtItems; ++i)
+        if (rw[i].ok) col[i] = xs[i];
+    }
+  }
+}
+
 // Pass 1: per tile and column, the tile aggregate (for the carry scan) and every lane's
 // exclusive (flag, sum) inside the tile, so that pass 3 needs no cross-lane work.
 __device__ __forceinline__ void store_lane_and_tile(int f, double s, int lane, int64_t slot, int64_t tslot,
@@ -151,12 +186,14 @@ __global__ void __launch_bounds__(256) k_leaf_agg(LeafParams p) {
 #pragma unroll
     for (int i = 0; i < kHtItems; ++i) rw[i] = leaf_row(p, e0 + i);
     for (int c = 0; c < p.N; ++c) {
+      double xs[kHtItems];
+      load_leaf_items(p, rw, e0, c, false, xs);
       int f = 0;
       double s = 0.0;
 #pragma unroll
       for (int i = 0; i < kHtItems; ++i) {
         if (!rw[i].ok) continue;
-        const double x = p.data[(int64_t)rw[i].src * p.rs + (int64_t)c * p.cs];
+        const double x = xs[i];
         if (rw[i].pos == 0) { f = 1; s = x; } else { s += x; }
       }
       const int64_t slot = (int64_t)c * p.n_tiles + t;
@@ -189,8 +226,7 @@ __global__ void __launch_bounds__(256, 2) k_leaf_emit(LeafParams p) {
       double run = fe ? se : p.tcarry[slot] + se;
       double* tcol = p.tails + (int64_t)c * p.ldt;
       double xs[kHtItems];                 // all loads first: the stores below may alias data
-#pragma unroll
-      for (int i = 0; i < kHtItems; ++i) xs[i] = rw[i].ok ? p.data[(int64_t)rw[i].src * p.rs + (int64_t)c * p.cs] : 0.0;
+      load_leaf_items(p, rw, e0, c, p.sdata != nullptr, xs);
 #pragma unroll
       for (int i = 0; i < kHtItems; ++i) {
         if (!rw[i].ok) continue;
@@ -206,7 +242,7 @@ __global__ void __launch_bounds__(256, 2) k_leaf_emit(LeafParams p) {
 
 // ------------------------------------------------------------------ mixed precision (v = 1)
 // Same three passes with the prefix sums in double-float arithmetic on the FP32 pipe: the
-// FP64 inputs are split exactly enough (2^-46) into float pairs, every running sum and
+// FP64 inputs are split exactly enough (2^-47) into float pairs, every running sum and
 // p a_p - S_p is formed in double-float, and the tail row is rounded once to float for
 // the FP32 TSQR leaf.  Heads stay float64.  Carries between lanes and tiles are kept in
 // float64 (one conversion per lane and column).
@@ -244,8 +280,7 @@ __global__ void __launch_bounds__(256) k_leaf_agg_mx(LeafParams p) {
     for (int i = 0; i < kHtItems; ++i) rw[i] = leaf_row(p, e0 + i);
     for (int c = 0; c < p.N; ++c) {
       double xs[kHtItems];
-#pragma unroll
-      for (int i = 0; i < kHtItems; ++i) xs[i] = rw[i].ok ? p.data[(int64_t)rw[i].src * p.rs + (int64_t)c * p.cs] : 0.0;
+      load_leaf_items(p, rw, e0, c, false, xs);
       int f = 0;
       dfl s{0.0f, 0.0f};
 #pragma unroll
@@ -277,11 +312,13 @@ __global__ void __launch_bounds__(256, 2) k_leaf_emit_mx(LeafParams p) {
     const int64_t e0 = t * kHtTile + (int64_t)lane * kHtItems;
     LeafRow rw[kHtItems];
     float gam[kHtItems];
+    dfl pos[kHtItems];
 #pragma unroll
     for (int i = 0; i < kHtItems; ++i) {
       rw[i] = leaf_row(p, e0 + i);
       const bool tail = rw[i].ok && rw[i].pos > 0;
       gam[i] = tail ? (float)(p.sq_phic[rw[i].g] * beta_at(p.beta, p.beta_len, rw[i].pos)) : 0.0f;
+      pos[i] = df_from_count(rw[i].pos);
     }
     for (int c = 0; c < p.N; ++c) {
       const int64_t slot = (int64_t)c * p.n_tiles + t;
@@ -290,15 +327,14 @@ __global__ void __launch_bounds__(256, 2) k_leaf_emit_mx(LeafParams p) {
       dfl run = df_from_double(fe ? se : p.tcarry[slot] + se);
       float* tcol = p.tails32 + (int64_t)c * p.ldt;
       double xs[kHtItems];
-#pragma unroll
-      for (int i = 0; i < kHtItems; ++i) xs[i] = rw[i].ok ? p.data[(int64_t)rw[i].src * p.rs + (int64_t)c * p.cs] : 0.0;
+      load_leaf_items(p, rw, e0, c, p.sdata != nullptr, xs);
 #pragma unroll
       for (int i = 0; i < kHtItems; ++i) {
         if (!rw[i].ok) continue;
         const dfl x = df_from_double(xs[i]);
         if (rw[i].pos == 0) run = dfl{0.0f, 0.0f};
         if (rw[i].pos > 0) {
-          const dfl d = df_add(df_mul(x, df_from_count(rw[i].pos)), df_neg(run));
+          const dfl d = df_add(df_mul(x, pos[i]), df_neg(run));
           tcol[e0 + i - rw[i].g - 1] = gam[i] * (d.hi + d.lo);
         }
         run = df_add(run, x);

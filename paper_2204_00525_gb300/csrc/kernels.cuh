@@ -37,6 +37,7 @@ struct NodeBuf {
   uint64_t* full;       // [M] full_join_size per group
   uint64_t* phic;       // [M] Phi_circ per group
   uint64_t* phid;       // [M] Phi_down per parent group
+  double* sq_phid;      // [M] sqrt(Phi_down) per parent group (the scales passed to the parent)
   uint64_t* phiu;       // [M] Phi_up per parent group
   uint64_t* theta_incl; // [M] inclusive prefix of theta over groups
   double* sq_phic;      // [M] sqrt(Phi_circ) per group
@@ -46,6 +47,8 @@ struct NodeBuf {
   double* fac;          // [M * (1 + n_children)] scale factors per group
   double* vw;           // [M * 3] v, W, gamma per group
   double* hf;           // [M] 1 / sqrt(Phi_down) per parent group
+  double* sdata;        // [lds x N_i] the data in sorted row order (lds = M rounded up to 8)
+  int64_t lds;
   // outputs
   double* heads;        // [M x N_i] col-major, ld M
   double* tails;        // [M x N_i] col-major, ld M  (rows M - G used)
@@ -83,6 +86,7 @@ struct ChildLink {
   const uint64_t* pkey;      // child's parent-group keys [P_c], strictly increasing
   const int32_t* sizes;      // child's sizes (P_c = sizes[1])
   const uint64_t* phid;      // child's Phi_down [P_c]
+  double* sq_phid;           // child's sqrt(Phi_down) [P_c] (written with the division below)
   uint64_t* phiu;            // child's Phi_up [P_c] (accumulated, then divided)
   int32_t* q;                // [G_i] out
   const double* data;        // child's table of heads passed up (leaf: heads, else data2)
@@ -113,6 +117,7 @@ struct CountParams {
   double* hf;
 };
 
+void counts_clear(NodeBuf& b, int64_t bound, cudaStream_t st, int64_t* launches);
 void counts_pass1(const CountParams& p, cudaStream_t st, int* err, int64_t* launches);
 void counts_pass2(const CountParams& p, cudaStream_t st, int* err, int64_t* launches);
 void counts_finalize_child(const ChildLink& c, int64_t bound, cudaStream_t st, int64_t* launches);
@@ -129,6 +134,8 @@ struct LeafParams {
   const double* data;
   int64_t rs, cs;            // element (input row r, column c) at data[r * rs + c * cs]
   const int32_t* perm;       // sorted position -> input row; null means identity
+  double* sdata;             // with perm: the data in sorted order, written by the first pass
+  int64_t lds;               //   and read back by the last (leading dimension lds, a multiple of 8)
   const int32_t* row_gid;
   const int32_t* goff;
   const double* sq_phic;

@@ -159,12 +159,6 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const uint64_t* key_in, c
   }
 }
 
-__global__ void k_radix_excl(const int32_t* counts, int32_t* incl, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    incl[i] -= counts[i];
-}
-
 int64_t radix_tiles(int64_t n) { return (n + kRsTile - 1) / kRsTile; }
 
 // The dynamic shared-memory limit is a property of the function, not of a launch: it is
@@ -189,11 +183,10 @@ int radix_sort(uint64_t* key[2], int32_t* perm[2], int64_t n, int bits, int32_t*
   for (int shift = 0; shift < bits; shift += width) {
     k_radix_hist<<<(unsigned)nt, 256, 0, st>>>(key[cur], n, shift, bins, hist, nt);
     ScanSrc src{SCAN_PLAIN_I32, hist, 0};
-    scan_inclusive<int32_t>(src, hist + hn, hn, nullptr, scan_tmp, st, launches);
-    k_radix_excl<<<grid_for(hn, 256), 256, 0, st>>>(hist, hist + hn, hn);
+    scan_exclusive_i32(src, hist + hn, hn, scan_tmp, st, launches);
     k_radix_scatter<<<(unsigned)nt, 256, smem, st>>>(key[cur], perm[cur], key[cur ^ 1], perm[cur ^ 1], n, shift,
                                                      bins, hist + hn, nt);
-    *launches += 3;
+    *launches += 2;
     cur ^= 1;
   }
   return cur;

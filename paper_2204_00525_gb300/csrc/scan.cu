@@ -84,7 +84,7 @@ __global__ void k_scan_tiles(int64_t n_max, const int32_t* n_dev, T* tile_sum) {
 
 template <typename T>
 __global__ void k_scan_apply(ScanSrc src, int64_t n_max, const int32_t* n_dev, const T* tile_off,
-                             T* out) {
+                             T* out, int exclusive) {
   const int64_t n = live_n(n_max, n_dev);
   const int64_t base = (int64_t)blockIdx.x * kScanTile;
   if (base >= n) return;
@@ -103,20 +103,32 @@ __global__ void k_scan_apply(ScanSrc src, int64_t n_max, const int32_t* n_dev, c
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     int64_t e = first + i;
-    ex += v[i];
-    if (e < n) out[e] = ex;
+    const T incl = ex + v[i];
+    if (e < n) out[e] = exclusive ? ex : incl;
+    ex = incl;
   }
+}
+
+template <typename T>
+static void scan_any(const ScanSrc& src, T* out, int64_t n_max, const int32_t* n_dev, T* tmp, int exclusive,
+                     cudaStream_t st, int64_t* launches) {
+  if (n_max <= 0) return;
+  const unsigned nt = (unsigned)scan_tiles(n_max);
+  k_scan_reduce<T><<<nt, kScanThreads, 0, st>>>(src, n_max, n_dev, tmp);
+  k_scan_tiles<T><<<1, kScanThreads, 0, st>>>(n_max, n_dev, tmp);
+  k_scan_apply<T><<<nt, kScanThreads, 0, st>>>(src, n_max, n_dev, tmp, out, exclusive);
+  if (launches) *launches += 3;
 }
 
 template <typename T>
 void scan_inclusive(const ScanSrc& src, T* out, int64_t n_max, const int32_t* n_dev, T* tmp,
                     cudaStream_t st, int64_t* launches) {
-  if (n_max <= 0) return;
-  const unsigned nt = (unsigned)scan_tiles(n_max);
-  k_scan_reduce<T><<<nt, kScanThreads, 0, st>>>(src, n_max, n_dev, tmp);
-  k_scan_tiles<T><<<1, kScanThreads, 0, st>>>(n_max, n_dev, tmp);
-  k_scan_apply<T><<<nt, kScanThreads, 0, st>>>(src, n_max, n_dev, tmp, out);
-  if (launches) *launches += 3;
+  scan_any<T>(src, out, n_max, n_dev, tmp, 0, st, launches);
+}
+
+void scan_exclusive_i32(const ScanSrc& src, int32_t* out, int64_t n_max, int32_t* tmp, cudaStream_t st,
+                        int64_t* launches) {
+  scan_any<int32_t>(src, out, n_max, nullptr, tmp, 1, st, launches);
 }
 
 template void scan_inclusive<int32_t>(const ScanSrc&, int32_t*, int64_t, const int32_t*, int32_t*,
