@@ -35,7 +35,6 @@ static int fail(int code, const std::string& msg) {
   } while (0)
 
 constexpr int kStages = 8;
-constexpr int64_t kBetaMax = 1 << 20;
 
 struct Node {
   int id = 0, parent = -1;
@@ -79,7 +78,7 @@ struct figaro_plan_s {
   size_t arena_bytes = 0;
   int* err_dev = nullptr;
   int* err_host = nullptr;             // pinned: [0] error word, [4 + 4 i ..] sizes of node i
-  double* beta = nullptr;
+  double2* beta = nullptr;
   int64_t beta_len = 0;
   std::vector<fig::TsqrBlock> blocks;
   fig::TsqrBlock* blocks_dev = nullptr;
@@ -141,8 +140,8 @@ static void layout(figaro_plan_s& P, Arena& a) {
   int64_t maxM = 1;
   for (auto& n : P.nodes) maxM = std::max(maxM, n.M);
   P.err_dev = a.take<int>(4);
-  P.beta_len = std::min<int64_t>(maxM + 1, kBetaMax);
-  P.beta = a.take<double>(P.beta_len);
+  P.beta_len = maxM + 1;                 // every position of every group: no fallback path
+  P.beta = a.take<double2>(P.beta_len);
   for (auto& n : P.nodes) {
     NodeBuf& b = n.b;
     const int64_t M = n.M;
@@ -747,7 +746,7 @@ static int enqueue_r(figaro_plan_s& P, double* R, int64_t ldr) {
     lp.lflag = n.b.lflag;
     lp.lsum = n.b.lsum;
     lp.n_tiles = n.n_tiles;
-    leaf_heads_tails(lp, s, &P.launches);
+    leaf_heads_tails(lp, n.b.sizes, s, &P.launches);
     FIG_CUDA(rec(P.ev_leaf[i], s));
     if (!serial && n.blk_tails >= 0) {
       const int rc = run_block(n.blk_tails, P.ev_leaf[i]);

@@ -76,14 +76,18 @@ __device__ __forceinline__ dfl df_from_count(int32_t p) {
 // (a carry into the exponent gives 2^30 = 2^29 + 64 * 2^23), and subtracting 2^29 is
 // exact (Sterbenz).  Outside |x| in [2^-74, 2^127] (zero, tiny or huge values) the FP64
 // conversion is used instead.
+// Out-of-line on purpose: inlined, the compiler if-converts this rare path and issues its
+// FP64 conversions for every element.
+__device__ __noinline__ dfl df_from_double_wide(double x) {
+  if (x == 0.0) return dfl{0.0f, 0.0f};
+  const float h = (float)x;
+  return dfl{h, (float)(x - (double)h)};
+}
+
 __device__ __forceinline__ dfl df_from_double(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int e = (int)((b >> 52) & 0x7FFull);
-  if (e < 949 || e > 1150) {
-    if ((b << 1) == 0ull) return dfl{0.0f, 0.0f};
-    const float h = (float)x;
-    return dfl{h, (float)(x - (double)h)};
-  }
+  if (e < 949 || e > 1150) return df_from_double_wide(x);
   const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
   const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
   const float h = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)(m >> 29));

@@ -40,17 +40,19 @@ __device__ __forceinline__ void pair_scan_incl(int& f, double& s, int lane) {
   }
 }
 
-__device__ __forceinline__ double beta_at(const double* beta, int64_t len, int64_t p) {
-  return p < len ? beta[p] : 1.0 / sqrt((double)p * ((double)p + 1.0));
-}
-
-__global__ void k_beta(double* beta, int64_t len) {
+// Per-position coefficients of the tail formula, {beta_p, p beta_p} with
+// beta_p = 1 / sqrt(p (p + 1)), for every position p of every group (the table's length
+// is the largest relation's row count + 1).  Read from memory rather than computed, so
+// that no FP64 conversion or square root is issued per row; FP64 issues slowly here.
+__global__ void k_beta(double2* beta, int64_t len) {
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < len;
-       p += (int64_t)gridDim.x * blockDim.x)
-    beta[p] = p == 0 ? 0.0 : 1.0 / sqrt((double)p * ((double)p + 1.0));
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const double b = p == 0 ? 0.0 : 1.0 / sqrt((double)p * ((double)p + 1.0));
+    beta[p] = make_double2(b, (double)p * b);
+  }
 }
 
-void beta_table(double* beta, int64_t len, cudaStream_t st) {
+void beta_table(double2* beta, int64_t len, cudaStream_t st) {
   k_beta<<<grid_for(len, 256, 4096), 256, 0, st>>>(beta, len);
 }
 
@@ -211,13 +213,14 @@ __global__ void __launch_bounds__(256, 2) k_leaf_emit(LeafParams p) {
   for (int64_t t = wid; t < p.n_tiles; t += nwarps) {
     const int64_t e0 = t * kHtTile + (int64_t)lane * kHtItems;
     LeafRow rw[kHtItems];
-    double gam[kHtItems], pd[kHtItems];
+    double ca[kHtItems], cb[kHtItems];    // tail = ca x - cb S: ca = g p beta_p, cb = g beta_p
 #pragma unroll
     for (int i = 0; i < kHtItems; ++i) {
       rw[i] = leaf_row(p, e0 + i);
-      const bool tail = rw[i].ok && rw[i].pos > 0;
-      gam[i] = tail ? p.sq_phic[rw[i].g] * beta_at(p.beta, p.beta_len, rw[i].pos) : 0.0;
-      pd[i] = (double)rw[i].pos;
+      const double2 bt = p.beta[rw[i].ok ? rw[i].pos : 0];
+      const double gs = rw[i].ok ? p.sq_phic[rw[i].g] : 0.0;
+      ca[i] = gs * bt.y;
+      cb[i] = gs * bt.x;
     }
     for (int c = 0; c < p.N; ++c) {
       const int64_t slot = (int64_t)c * p.n_tiles + t;
@@ -232,9 +235,9 @@ __global__ void __launch_bounds__(256, 2) k_leaf_emit(LeafParams p) {
         if (!rw[i].ok) continue;
         const double x = xs[i];
         if (rw[i].pos == 0) run = 0.0;
-        if (rw[i].pos > 0) tcol[e0 + i - rw[i].g - 1] = gam[i] * fma(pd[i], x, -run);
+        if (rw[i].pos > 0) tcol[e0 + i - rw[i].g - 1] = fma(ca[i], x, -(cb[i] * run));
         run += x;
-        if (rw[i].last) p.heads[(int64_t)c * p.ldh + rw[i].g] = run * p.hrow[rw[i].g];
+        if (rw[i].last) p.heads[(int64_t)c * p.ldh + rw[i].g] = run;   // group sum; scaled by heads_finish
       }
     }
   }
@@ -317,7 +320,7 @@ __global__ void __launch_bounds__(256, 2) k_leaf_emit_mx(LeafParams p) {
     for (int i = 0; i < kHtItems; ++i) {
       rw[i] = leaf_row(p, e0 + i);
       const bool tail = rw[i].ok && rw[i].pos > 0;
-      gam[i] = tail ? (float)(p.sq_phic[rw[i].g] * beta_at(p.beta, p.beta_len, rw[i].pos)) : 0.0f;
+      gam[i] = tail ? (float)(p.sq_phic[rw[i].g] * p.beta[rw[i].pos].x) : 0.0f;
       pos[i] = df_from_count(rw[i].pos);
     }
     for (int c = 0; c < p.N; ++c) {
@@ -338,7 +341,10 @@ __global__ void __launch_bounds__(256, 2) k_leaf_emit_mx(LeafParams p) {
           tcol[e0 + i - rw[i].g - 1] = gam[i] * (d.hi + d.lo);
         }
         run = df_add(run, x);
-        if (rw[i].last) p.heads[(int64_t)c * p.ldh + rw[i].g] = df_to_double(run) * p.hrow[rw[i].g];
+        // the pair's bits, combined and scaled by heads_finish (a conversion here would be
+        // if-converted and issued for every element)
+        if (rw[i].last)
+          p.heads[(int64_t)c * p.ldh + rw[i].g] = __hiloint2double(__float_as_int(run.hi), __float_as_int(run.lo));
       }
     }
   }
@@ -352,7 +358,22 @@ static unsigned ht_grid(int64_t n_tiles) {
   return (unsigned)blocks;
 }
 
-void leaf_heads_tails(const LeafParams& p, cudaStream_t st, int64_t* launches) {
+// Head of every group: the group sum written by the last pass (a float pair's bits on
+// the mixed path) times 1 / sqrt(rows).
+__global__ void k_heads_finish(LeafParams p, const int32_t* sizes, int mixed) {
+  const int64_t G = sizes[0];
+  const int64_t total = G * p.N;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = k / G, g = k - c * G;
+    double* h = p.heads + c * p.ldh + g;
+    double s = *h;
+    if (mixed) s = (double)__int_as_float(__double2hiint(s)) + (double)__int_as_float(__double2loint(s));
+    *h = s * p.hrow[g];
+  }
+}
+
+void leaf_heads_tails(const LeafParams& p, const int32_t* sizes, cudaStream_t st, int64_t* launches) {
   if (p.N == 0) return;
   const unsigned g = ht_grid(p.n_tiles);
   if (p.tails32) k_leaf_agg_mx<<<g, 256, 0, st>>>(p);
@@ -360,7 +381,8 @@ void leaf_heads_tails(const LeafParams& p, cudaStream_t st, int64_t* launches) {
   k_tile_carry<<<p.N, kCarryThreads, 0, st>>>(p.tflag, p.tsum, p.tcarry, p.n_tiles, nullptr);
   if (p.tails32) k_leaf_emit_mx<<<g, 256, 0, st>>>(p);
   else k_leaf_emit<<<g, 256, 0, st>>>(p);
-  *launches += 3;
+  k_heads_finish<<<grid_for(p.M * (int64_t)p.N, 256, 152 * 8), 256, 0, st>>>(p, sizes, p.tails32 != nullptr);
+  *launches += 4;
 }
 
 // ------------------------------------------------------------------ join + projection
@@ -462,7 +484,7 @@ __global__ void __launch_bounds__(256, 2) k_gen_emit(GenParams p) {
         if (rw[i].k == 0) run = 0.0;
         if (rw[i].k > 0) p.gtails[(int64_t)c * p.M + rw[i].trow] = fma(gw[i], D, -gv[i] * run);
         run = fma(rw[i].v, D, run);
-        if (rw[i].last) p.data2[(int64_t)c * p.M + rw[i].pg] = run * p.hf[rw[i].pg];
+        if (rw[i].last) p.data2[(int64_t)c * p.M + rw[i].pg] = run;   // scaled by gen_heads_finish
       }
     }
   }
@@ -479,6 +501,17 @@ __global__ void k_root_rows(GenParams p) {
   }
 }
 
+// Generalized head of every X_p group: the weighted group sum times 1 / sqrt(Phi_down).
+__global__ void k_gen_heads_finish(GenParams p) {
+  const int64_t P = p.sizes[1];
+  const int64_t total = P * p.N;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = k / P, q = k - c * P;
+    p.data2[c * p.M + q] *= p.hf[q];
+  }
+}
+
 void gen_heads_tails(const GenParams& p, cudaStream_t st, int64_t* launches) {
   if (p.is_root) {
     k_root_rows<<<grid_for(p.M * (int64_t)p.N, 256, 152 * 16), 256, 0, st>>>(p);
@@ -489,7 +522,8 @@ void gen_heads_tails(const GenParams& p, cudaStream_t st, int64_t* launches) {
   k_gen_agg<<<g, 256, 0, st>>>(p);
   k_tile_carry<<<p.N, kCarryThreads, 0, st>>>(p.tflag, p.tsum, p.tcarry, p.n_tiles, p.sizes);
   k_gen_emit<<<g, 256, 0, st>>>(p);
-  *launches += 3;
+  k_gen_heads_finish<<<grid_for(p.M * (int64_t)p.N, 256, 152 * 8), 256, 0, st>>>(p);
+  *launches += 4;
 }
 
 }  // namespace fig

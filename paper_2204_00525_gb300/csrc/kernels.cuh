@@ -140,7 +140,7 @@ struct LeafParams {
   const int32_t* goff;
   const double* sq_phic;
   const double* hrow;
-  const double* beta;        // beta[p] = 1 / sqrt(p (p + 1))
+  const double2* beta;       // {beta_p, p beta_p}, beta_p = 1 / sqrt(p (p + 1)), every position p < M
   int64_t beta_len;
   double* tails;
   int64_t ldt;
@@ -183,8 +183,8 @@ struct GenParams {
   int is_root;
 };
 
-void beta_table(double* beta, int64_t len, cudaStream_t st);
-void leaf_heads_tails(const LeafParams& p, cudaStream_t st, int64_t* launches);
+void beta_table(double2* beta, int64_t len, cudaStream_t st);
+void leaf_heads_tails(const LeafParams& p, const int32_t* sizes, cudaStream_t st, int64_t* launches);
 void gen_heads_tails(const GenParams& p, cudaStream_t st, int64_t* launches);
 
 // ------------------------------------------------------------------ tsqr.cu

@@ -90,10 +90,13 @@ __global__ void __launch_bounds__(kQrThreads) k_tsqr_cta(TsqrBlock b, const doub
     if (!tri_in) {
       const int64_t r0 = t * b.tile;
       m = (int)((rows - r0) < b.tile ? (rows - r0) : b.tile);
-      for (int c = 0; c < n; ++c)
-        for (int i = threadIdx.x; i < m; i += blockDim.x)
-          A[(int64_t)c * lda + i] = b.ptr32 ? (E)b.ptr32[(int64_t)c * b.ld + r0 + i]
-                                            : (E)b.ptr[(int64_t)c * b.ld + r0 + i];
+      if (b.ptr32) {
+        for (int c = 0; c < n; ++c)
+          for (int i = threadIdx.x; i < m; i += blockDim.x) A[(int64_t)c * lda + i] = (E)b.ptr32[(int64_t)c * b.ld + r0 + i];
+      } else {
+        for (int c = 0; c < n; ++c)
+          for (int i = threadIdx.x; i < m; i += blockDim.x) A[(int64_t)c * lda + i] = (E)b.ptr[(int64_t)c * b.ld + r0 + i];
+      }
     } else {
       const int64_t first = t * b.fan;
       const int cnt = (int)((nt_in - first) < b.fan ? (nt_in - first) : b.fan);

@@ -168,13 +168,21 @@ __global__ void __launch_bounds__(128) k_tsqr_reg(TsqrBlock b, const double* tri
     if (!tri_in) {
       const int64_t r0 = t * TW;
       m = (int)((rows - r0) < TW ? (rows - r0) : TW);
+      // uniform branch on the source type: no conversion of the unused source is issued
+      if (b.ptr32) {
 #pragma unroll
-      for (int r = 0; r < RPL; ++r) {
-        const int i = lane + 32 * r;
+        for (int r = 0; r < RPL; ++r) {
+          const int i = lane + 32 * r;
 #pragma unroll
-        for (int c = 0; c < N; ++c)
-          a[r][c] = (i < m && c < n) ? (b.ptr32 ? (E)b.ptr32[(int64_t)c * b.ld + r0 + i]
-                                                : (E)b.ptr[(int64_t)c * b.ld + r0 + i]) : E(0);
+          for (int c = 0; c < N; ++c) a[r][c] = (i < m && c < n) ? (E)b.ptr32[(int64_t)c * b.ld + r0 + i] : E(0);
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+          const int i = lane + 32 * r;
+#pragma unroll
+          for (int c = 0; c < N; ++c) a[r][c] = (i < m && c < n) ? (E)b.ptr[(int64_t)c * b.ld + r0 + i] : E(0);
+        }
       }
     } else {
       const int64_t first = t * b.fan;
