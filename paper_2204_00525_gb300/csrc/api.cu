@@ -484,6 +484,7 @@ static void make_blocks(figaro_plan_s& P) {
       TsqrBlock t{};
       t.n = n.N_sub;
       t.kind = BLK_GEN;
+      t.prio = true;
       t.M = n.M;
       t.bound = n.M;
       tsqr_plan_block(t, mixed);
@@ -495,6 +496,7 @@ static void make_blocks(figaro_plan_s& P) {
       TsqrBlock t{};
       t.n = n.N_sub;
       t.kind = BLK_ROOT;
+      t.prio = true;
       t.M = n.M;
       t.bound = n.M;
       tsqr_plan_block(t, mixed);
@@ -1014,8 +1016,9 @@ int figaro_plan(const figaro_join_tree* tree, const figaro_options* opt, void* s
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->join_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->join_out, cudaEventDisableTiming);
   if (e != cudaSuccess) return bail(e, "cudaEventCreate");
-  // the TSQR block streams get the lowest priority: their persistent kernels yield SMs to
-  // the relation and main streams, which carry the longer dependency chain
+  // The tails blocks' TSQR streams get the lowest priority (long FP64 work that fills the
+  // gaps); the relation and main streams and the generalized-tail / root blocks, which
+  // form the dependency chain to R, get the highest.
   int prio_lo = 0, prio_hi = 0;
   e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
   if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&P->exec, cudaStreamNonBlocking, prio_hi);
@@ -1023,7 +1026,7 @@ int figaro_plan(const figaro_join_tree* tree, const figaro_options* opt, void* s
   P->side.assign(P->blocks.size(), nullptr);
   P->side_done.assign(P->blocks.size(), nullptr);
   for (size_t bi = 0; bi < P->blocks.size(); ++bi) {
-    e = cudaStreamCreateWithPriority(&P->side[bi], cudaStreamNonBlocking, prio_lo);
+    e = cudaStreamCreateWithPriority(&P->side[bi], cudaStreamNonBlocking, P->blocks[bi].prio ? prio_hi : prio_lo);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->side_done[bi], cudaEventDisableTiming);
     if (e != cudaSuccess) return bail(e, "side streams");
   }

@@ -78,7 +78,7 @@ __device__ __forceinline__ dfl df_from_count(int32_t p) {
 // conversion is used instead.
 // Out-of-line on purpose: inlined, the compiler if-converts this rare path and issues its
 // FP64 conversions for every element.
-__device__ __noinline__ dfl df_from_double_wide(double x) {
+static __device__ __noinline__ dfl df_from_double_wide(double x) {
   if (x == 0.0) return dfl{0.0f, 0.0f};
   const float h = (float)x;
   return dfl{h, (float)(x - (double)h)};

@@ -204,9 +204,9 @@ struct TsqrBlock {
   int levels;                // reduce levels after the leaf
   double* tri[2];            // ping-pong triangle buffers [bound tiles x n x n]
   int top;                   // buffer holding the last level
-  int nreg;                  // register path: columns padded to an even count <= 16; 0 = not used
-  int nw;                    // shared-memory warp path: columns padded to 8, 16 or 32; 0 = not used
-  int wpc;                   // warp path: warps (tiles) per thread block
+  int nreg;                  // register (warp-per-tile) path: padded column count; 0 = not used
+  int64_t warp_min;          // register path: levels with at least this many tiles (else block-per-tile)
+  bool prio;                 // on the critical path: its stream gets the high priority
   const int* cols;           // device [n]: global column of each block column
   void* scratch;             // block path: global tile slots when a tile exceeds shared memory
 };

@@ -22,7 +22,8 @@
 
 namespace fig {
 
-constexpr int kQrThreads = 256;
+constexpr int kQrThreads = 256;   // 8 warps: hh_small's row classes
+constexpr int kRedElems = 320;     // reduction scratch ahead of the tile in shared memory
 constexpr size_t kSmemCap = 200 * 1024;
 
 // ------------------------------------------------------------------ block path (n > 32)
@@ -68,21 +69,87 @@ __device__ void hh_qr(E* A, int lda, int m, int n, E* red) {
   }
 }
 
+// ------------------------------------------------------------------ narrow tiles (n <= 32)
+constexpr int kSmallRed = 8 * 32 + 32 + 8;   // per-warp partial dot products, w, scalars
+
+// Householder QR of an m x n tile (n <= 32, column-major in shared memory) by 8 warps,
+// shaped for latency: per step one pass of dot products d_j = sum_{i>k} a_ik a_ij
+// (j >= k, d_k = sigma) with lane = column and warp = row class, a three-level tree over
+// the warps, the scalars in warp 0, and one update pass a_ij -= w_j a_ik with
+// w_j = tau (v0 a_kj + d_j); row k becomes a_kj - w_j v0 and a_kk = beta.
+template <typename E>
+__device__ void hh_small(E* A, int lda, int m, int n, E* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  E* part = red;               // [8][32]
+  E* w = red + 256;            // [32]
+  E* sc = red + 288;           // v0
+  const int kmax = m < n ? m : n;
+  for (int k = 0; k < kmax; ++k) {
+    const int j = k + lane;
+    const E* ak = A + (int64_t)k * lda;
+    E d = 0;
+    if (j < n) {
+      const E* aj = A + (int64_t)j * lda;
+      for (int i = k + 1 + warp; i < m; i += 8) d = fma(ak[i], aj[i], d);
+    }
+    part[warp * 32 + lane] = d;
+    __syncthreads();
+    if (warp < 4) part[warp * 32 + lane] += part[(warp + 4) * 32 + lane];
+    __syncthreads();
+    if (warp < 2) part[warp * 32 + lane] += part[(warp + 2) * 32 + lane];
+    __syncthreads();
+    if (warp == 0) {
+      const E dj = part[lane] + part[32 + lane];
+      const E sigma = __shfl_sync(0xffffffffu, dj, 0);
+      E wj = 0;
+      if (sigma != E(0)) {                       // warp-uniform
+        const E alpha = ak[k];
+        const bool mine = j < n && lane > 0;
+        E* aj = A + (int64_t)(mine ? j : k) * lda;
+        const E akj = mine ? aj[k] : E(0);
+        __syncwarp();                            // every read of row k before its writes
+        E beta, v0, tau;
+        HhScalars<E>::get(alpha, sigma, beta, v0, tau);
+        if (mine) {
+          wj = tau * fma(v0, akj, dj);
+          aj[k] = akj - wj * v0;
+        }
+        if (lane == 0) A[(int64_t)k * lda + k] = beta;
+      }
+      w[lane] = wj;
+      if (lane == 0) sc[0] = sigma;
+    }
+    __syncthreads();
+    if (sc[0] != E(0) && lane > 0 && j < n) {
+      const E wj = w[lane];
+      E* aj = A + (int64_t)j * lda;
+      for (int i = k + 1 + warp; i < m; i += 8) aj[i] = fma(-wj, ak[i], aj[i]);
+    }
+    __syncthreads();
+  }
+}
+
+// Leading dimension of a tile in the block kernel: the tile's row count rounded up to an
+// odd number, so that hh_small's lanes (one column each) fall in distinct banks.
+__host__ __device__ __forceinline__ int cta_lda(const TsqrBlock& b, bool tree) {
+  return (tree ? b.fan * b.n : b.tile) | 1;
+}
+
 // One thread block per tile (persistent).  The tile sits in shared memory, or in a
 // global scratch slot per block when it does not fit.
 // With few_only set (tree levels that the warp-per-tile kernel also serves) it works only
-// on levels with fewer than kWarpModeTiles tiles.
+// on levels with fewer than b.warp_min tiles.
 template <typename E>
 __global__ void __launch_bounds__(kQrThreads) k_tsqr_cta(TsqrBlock b, const double* tri_in, double* tri_out,
                                                          int64_t div_in, E* gscratch, int few_only) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int64_t rows = block_rows(b);
   if (copy_single(b, rows, div_in, tri_in, tri_out)) return;
-  if (few_only && level_tiles(b, rows, div_in, tri_in == nullptr) >= kWarpModeTiles) return;
+  if (few_only && level_tiles(b, rows, div_in, tri_in == nullptr) >= b.warp_min) return;
   const int n = b.n;
-  const int lda = tri_in ? b.fan * n : b.tile;
+  const int lda = cta_lda(b, tri_in != nullptr);
   E* red = reinterpret_cast<E*>(smem_raw);
-  E* A = gscratch ? gscratch + (int64_t)blockIdx.x * lda * n : red + 64;
+  E* A = gscratch ? gscratch + (int64_t)blockIdx.x * lda * n : red + kRedElems;
   const int64_t nt_in = tri_in ? (rows + div_in - 1) / div_in : 0;
   const int64_t n_tiles = level_tiles(b, rows, div_in, tri_in == nullptr);
   for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
@@ -108,7 +175,8 @@ __global__ void __launch_bounds__(kQrThreads) k_tsqr_cta(TsqrBlock b, const doub
       }
     }
     __syncthreads();
-    hh_qr<E>(A, lda, m, n, red);
+    if (n <= 32 && m <= 96) hh_small<E>(A, lda, m, n, red);   // short tiles: latency-shaped
+    else hh_qr<E>(A, lda, m, n, red);
     double* tri = tri_out + t * n * n;
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
       const int c = idx / n, r = idx - c * n;
@@ -168,21 +236,23 @@ static int reg_tile_of(int N) {
   }
 }
 
-static size_t cta_smem(int lda, int n, size_t esz) { return (64 + (size_t)lda * n) * esz; }
+static size_t cta_smem(int lda, int n, size_t esz) { return (kRedElems + (size_t)lda * n) * esz; }
 
 void tsqr_plan_block(TsqrBlock& b, bool mixed) {
   const int n = b.n;
   const size_t esz = mixed ? sizeof(float) : sizeof(double);
   b.nreg = reg_class(n);
-  b.nw = 0;
   if (b.nreg) {
-    b.wpc = 4;
+    // one warp's QR of a tile costs about N^2 FP64 instructions at ~70 cycles each: for
+    // N <= 16 (tiles of 128-256 rows) it beats a thread block per tile from two tiles
+    // on; wider tiles (64 rows) keep the block kernel until the level fills the GPU
+    b.warp_min = b.nreg <= 16 ? 2 : 152 * 4;
     b.tile = reg_tile_of(b.nreg);
     // n <= 16: tree tiles fill a register tile (fan = TW / n >= 4); wider blocks reduce
     // their trees with the block-per-tile kernel only, six triangles at a time
     b.fan = b.nreg <= 16 ? b.tile / n : 6;
   } else {
-    b.wpc = 0;
+    b.warp_min = 0;
     int64_t t = (int64_t)(64 * 1024 / (esz * n));
     t = (t / 32) * 32;
     if (t > 2048) t = 2048;
@@ -215,9 +285,9 @@ int64_t tsqr_scratch_elems(const TsqrBlock& b, bool mixed) {
   const size_t esz = mixed ? sizeof(float) : sizeof(double);
   int64_t need = 0;
   const int64_t grid = 152 * 2;
-  if (cta_smem(b.tile, b.n, esz) > kSmemCap) need = grid * b.tile * b.n;
-  if (cta_smem(b.fan * b.n, b.n, sizeof(double)) > kSmemCap) {
-    const int64_t r = grid * (int64_t)b.fan * b.n * b.n;
+  if (cta_smem(cta_lda(b, false), b.n, esz) > kSmemCap) need = grid * (int64_t)cta_lda(b, false) * b.n;
+  if (cta_smem(cta_lda(b, true), b.n, esz) > kSmemCap) {
+    const int64_t r = grid * (int64_t)cta_lda(b, true) * b.n;
     if (r > need) need = r;
   }
   return need;
@@ -226,11 +296,11 @@ int64_t tsqr_scratch_elems(const TsqrBlock& b, bool mixed) {
 template <typename E>
 static void launch_cta(const TsqrBlock& b, const double* tri_in, double* tri_out, int64_t div_in, int64_t tiles,
                        void* scratch, cudaStream_t st, int few_only = 0) {
-  const int lda = tri_in ? b.fan * b.n : b.tile;
+  const int lda = cta_lda(b, tri_in != nullptr);
   size_t smem = cta_smem(lda, b.n, sizeof(E));
   E* gs = nullptr;
   if (smem > kSmemCap) {
-    smem = 64 * sizeof(E);
+    smem = kRedElems * sizeof(E);
     gs = static_cast<E*>(scratch);
   }
   int64_t blocks = tiles < 1 ? 1 : tiles;

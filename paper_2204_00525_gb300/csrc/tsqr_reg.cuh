@@ -35,6 +35,55 @@ __device__ __forceinline__ bool copy_single(const TsqrBlock& b, int64_t rows, in
   return true;
 }
 
+// ------------------------------------------------------------------ Householder scalars
+// Scalars of one Householder step: the reflector maps x = (alpha, a_{k+1..m-1,k}) with
+// sigma = sum_{i>k} a_ik^2 to (beta, 0, ..., 0): nu = ||x||, beta = -sign(alpha) nu,
+// v0 = alpha - beta (v = (v0, a_{k+1..m-1,k}) unnormalised) and
+// tau = 2 / (v^T v) = 1 / (nu (nu + |alpha|)).
+template <typename E>
+struct HhScalars {
+  __device__ static void get(E alpha, E sigma, E& beta, E& v0, E& tau) {
+    const E nu = sqrt(fma(alpha, alpha, sigma));
+    beta = alpha >= E(0) ? -nu : nu;
+    v0 = alpha - beta;
+    tau = E(1) / (nu * (nu + fabs(alpha)));
+  }
+};
+
+// Double precision: FP64 instructions issue about once per 70 cycles per warp here, so the
+// square root and the reciprocal are formed by Newton-Raphson iterations from float
+// hardware approximations (relative error below 2^-22): y <- y (3/2 - t y^2 / 2) for
+// 1 / sqrt(t) and r <- r (2 - d r) for 1 / d, two steps each (quadratic convergence; a
+// measured sweep gives at most 4e-16 relative error for nu and 1e-15 for tau).  Outside
+// the range where the float seeds are accurate the plain operations are used.
+static __device__ __noinline__ void hh_scalars_wide(double alpha, double sigma, double& nu, double& tau) {
+  nu = sqrt(fma(alpha, alpha, sigma));
+  tau = 1.0 / (nu * (nu + fabs(alpha)));
+}
+
+template <>
+struct HhScalars<double> {
+  __device__ static void get(double alpha, double sigma, double& beta, double& v0, double& tau) {
+    const double t = fma(alpha, alpha, sigma);
+    double nu;
+    if (t > 1e-30 && t < 1e30) {
+      double y = (double)rsqrtf((float)t);
+      const double ht = 0.5 * t;
+      y = y * fma(-ht * y, y, 1.5);
+      y = y * fma(-ht * y, y, 1.5);
+      nu = t * y;
+      const double d = nu * (nu + fabs(alpha));
+      double r = (double)__frcp_rn((float)d);
+      r = r * fma(-d, r, 2.0);
+      tau = r * fma(-d, r, 2.0);
+    } else {
+      hh_scalars_wide(alpha, sigma, nu, tau);
+    }
+    beta = alpha >= 0.0 ? -nu : nu;
+    v0 = alpha - beta;
+  }
+};
+
 // ------------------------------------------------------------------ multi-value warp sum
 // Sum NW per-lane values over the warp by recursive halving: at the level with lane
 // offset o the lane keeps half of its values (the upper half if lane & o) and adds the
@@ -93,6 +142,14 @@ struct Pow2 {
   static constexpr int v = C <= 1 ? 1 : C <= 2 ? 2 : C <= 4 ? 4 : C <= 8 ? 8 : C <= 16 ? 16 : 32;
 };
 
+template <int P2>
+struct Log2 {
+  static constexpr int v = P2 <= 1 ? 0 : P2 <= 2 ? 1 : P2 <= 4 ? 2 : P2 <= 8 ? 3 : P2 <= 16 ? 4 : 5;
+};
+
+// One step.  After the multi-value sum, the lanes holding value t (t >= 1) form
+// w_t = tau (v0 a_Kt + d_t) together (one FMA and one multiply for all columns), and row
+// K joins the update of the rows below with x_K = v0, so every column costs RPL FMAs.
 template <typename E, int N, int RPL, int K>
 __device__ __forceinline__ void reg_hh_step(E (&a)[RPL][N], int m, int lane) {
   constexpr int C = N - K;
@@ -115,18 +172,22 @@ __device__ __forceinline__ void reg_hh_step(E (&a)[RPL][N], int m, int lane) {
   if (sig == E(0)) return;                   // uniform: column already reduced below K
   constexpr int kr = K / 32, kl = K % 32;    // lane and slot holding row K
   const E alpha = __shfl_sync(0xffffffffu, a[kr][K], kl);
-  const E normx = sqrt(fma(alpha, alpha, sig));
-  const E beta = alpha >= E(0) ? -normx : normx;
-  const E v0 = alpha - beta;
-  const E tau = E(1) / (normx * (normx + fabs(alpha)));
+  E beta, v0, tau;
+  HhScalars<E>::get(alpha, sig, beta, v0, tau);
+  const int my_t = lane >> (5 - Log2<P2>::v);   // the value this lane holds
+  E akt = E(0);
 #pragma unroll
   for (int t = 1; t < C; ++t) {
-    const E dt = __shfl_sync(0xffffffffu, mine, lane_of_value<P2>(t));
-    const E akj = __shfl_sync(0xffffffffu, a[kr][K + t], kl);
-    const E w = tau * fma(v0, akj, dt);
+    const E v = __shfl_sync(0xffffffffu, a[kr][K + t], kl);
+    if (my_t == t) akt = v;
+  }
+  const E w_mine = tau * fma(v0, akt, mine);
+  if (lane == kl) x[kr] = v0;
+#pragma unroll
+  for (int t = 1; t < C; ++t) {
+    const E w = __shfl_sync(0xffffffffu, w_mine, lane_of_value<P2>(t));
 #pragma unroll
     for (int r = 0; r < RPL; ++r) a[r][K + t] = fma(-w, x[r], a[r][K + t]);
-    if (lane == kl) a[kr][K + t] = akj - w * v0;
   }
   if (lane == kl) a[kr][K] = beta;
 }
@@ -145,13 +206,16 @@ struct RegQR<E, N, RPL, N> {
 };
 
 // Every level (leaf or tree) of a block with <= 32 columns runs two kernels: this one (one
-// warp per tile) works only when the level has at least kWarpModeTiles tiles; the
+// warp per tile) works only when the level has at least b.warp_min tiles; the
 // block-per-tile kernel takes the levels with fewer tiles, where the latency of one
-// warp's QR would dominate.
-constexpr int64_t kWarpModeTiles = 152 * 4;
+// warp's QR would dominate.  (The live tile count is known only on the device.)
+// Two warps per block: with ~190 registers per thread, 64-thread blocks pack 10 warps on
+// an SM where 128-thread blocks fit 8 (every FP64 instruction keeps its SM sub-partition
+// busy for tens of cycles, so resident warps are what keeps the FP64 pipe fed).
+constexpr int kRegThreads = 64;
 
 template <typename E, int N>
-__global__ void __launch_bounds__(128) k_tsqr_reg(TsqrBlock b, const double* tri_in, double* tri_out,
+__global__ void __launch_bounds__(kRegThreads) k_tsqr_reg(TsqrBlock b, const double* tri_in, double* tri_out,
                                                   int64_t div_in) {
   constexpr int RPL = RegCfg<N>::RPL, TW = RegCfg<N>::TW;
   const int lane = threadIdx.x & 31;
@@ -161,7 +225,7 @@ __global__ void __launch_bounds__(128) k_tsqr_reg(TsqrBlock b, const double* tri
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t nt_in = tri_in ? (rows + div_in - 1) / div_in : 0;
   const int64_t n_tiles = level_tiles(b, rows, div_in, tri_in == nullptr);
-  if (n_tiles < kWarpModeTiles) return;               // the block-per-tile kernel takes it
+  if (n_tiles < b.warp_min) return;                   // the block-per-tile kernel takes it
   for (int64_t t = gw; t < n_tiles; t += nw) {
     E a[RPL][N];
     int m;
@@ -214,20 +278,21 @@ __global__ void __launch_bounds__(128) k_tsqr_reg(TsqrBlock b, const double* tri
 template <typename E, int N>
 void launch_reg(const TsqrBlock& b, const double* tri_in, double* tri_out, int64_t div_in, int64_t tiles,
                 cudaStream_t st) {
-  // persistent: as many 4-warp blocks as are resident at once (registers decide), so that
+  // persistent: as many blocks as are resident at once (registers decide), so that
   // no second, partial wave of blocks runs at low occupancy
   static int resident = 0;
   if (resident == 0) {
     int per_sm = 0, sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tsqr_reg<E, N>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tsqr_reg<E, N>, kRegThreads, 0);
     resident = (per_sm > 0 && sms > 0) ? per_sm * sms : 152 * 4;
   }
-  int64_t blocks = (tiles + 3) / 4;
+  constexpr int wpb = kRegThreads / 32;
+  int64_t blocks = (tiles + wpb - 1) / wpb;
   if (blocks > resident) blocks = resident;
   if (blocks < 1) blocks = 1;
-  k_tsqr_reg<E, N><<<(unsigned)blocks, 128, 0, st>>>(b, tri_in, tri_out, div_in);
+  k_tsqr_reg<E, N><<<(unsigned)blocks, kRegThreads, 0, st>>>(b, tri_in, tri_out, div_in);
 }
 
 // Dispatch on the padded column count b.nreg; defined in tsqr_reg_f64.cu / tsqr_reg_f32.cu.
