@@ -39,6 +39,10 @@ WORKLOAD = ("path3_2m: R1(a;x1..x8) - R2(a,b;y1..y8) - R3(b;z1..z8), 2,000,000 r
 ROWS = 2_000_000
 SAMPLE_ROWS = 100_000          # oracle sample per relation (same shape and key distribution)
 FP64_PEAK_TFLOPS = 152 * 2070e6 * 4 / 1e12   # 152 SMs x 2.07 GHz x 2 DFMA/clk/SM x 2 flop
+# DRAM bytes per input row of the dominant kernel (k_tsqr_reg<double, 8>, leaf of a tails
+# block), from the ncu capture summarised in profiles/tsqr_reg8_fp64_path3_2m.md:
+# (dram__bytes_read.sum + dram__bytes_write.sum) / rows = 131.99 MB / 1,998,000 rows.
+DOMINANT_DRAM_BYTES_PER_ROW = 131.99e6 / 1_998_000
 
 
 def log(*a):
@@ -203,6 +207,7 @@ def run_figaro(args):
     pst._R = torch.empty(db.n_cols, db.n_cols, dtype=torch.float64, device="cuda")
     ms_staged = time_steps(pst, torch, args.steps, args.warmup, barrier)
     stages = pst.stage_times()
+    block_times = pst.block_times()
     pst.close()
 
     # --- mixed path
@@ -242,15 +247,27 @@ def run_figaro(args):
     launches = {k: v[1] / steps_timed for k, v in stages.items()}
     dom = max((k for k in per_stage if k != "tsqr_leaf"), key=per_stage.get)
     leaf_ms = per_stage["tsqr_leaf"]
-    leaf_tflops = info["tsqr_leaf_flops"] / (leaf_ms * 1e-3) / 1e12 if leaf_ms > 0 else None
-    roofline = {"kernel": "k_tsqr_reg<double,N> (TSQR leaf tiles: warp-per-tile Householder in registers, FP64)",
-                "bound": "alu", "achieved": leaf_tflops, "peak": round(FP64_PEAK_TFLOPS, 3),
-                "unit": "TFLOP/s", "frac": (leaf_tflops / FP64_PEAK_TFLOPS) if leaf_tflops else None,
-                "traffic": None,
+    # the dominant kernel: the register TSQR leaf of the 8-column tails blocks (one launch
+    # per block per step, timed by CUDA events around it on its stream in the stage-timed
+    # plan).  Algorithmic flops per launch: 2 rows n^2 - 2/3 n^3 (Householder, R only).
+    dom_blocks = [(ms / steps_timed, n, rows) for ms, n, rows in block_times if n == 8 and rows > 0]
+    dom_flops = sum(2.0 * rows * n * n - 2.0 / 3.0 * n ** 3 for _, n, rows in dom_blocks) / len(dom_blocks)
+    dom_ms = sum(ms for ms, _, _ in dom_blocks) / len(dom_blocks)
+    dom_rows = sum(rows for _, _, rows in dom_blocks) / len(dom_blocks)
+    dom_tflops = dom_flops / (dom_ms * 1e-3) / 1e12
+    roofline = {"kernel": "k_tsqr_reg<double, 8> (TSQR leaf of a tails block: warp-per-tile Householder "
+                          "in registers, FP64)",
+                "bound": "alu", "achieved": dom_tflops, "peak": round(FP64_PEAK_TFLOPS, 3),
+                "unit": "TFLOP/s", "frac": dom_tflops / FP64_PEAK_TFLOPS,
+                "traffic": DOMINANT_DRAM_BYTES_PER_ROW * dom_rows,
                 "peak_kind": "derived FP64 pipe peak: 152 SMs x 2 DFMA/clk x 2070 MHz",
-                "flops_per_step": info["tsqr_leaf_flops"], "launches_per_step": launches["tsqr_leaf"],
-                "leaf_ms_per_step": leaf_ms, "staged_ms_per_step": ms_staged,
-                "largest_stage": dom}
+                "flops_per_launch": dom_flops, "rows_per_launch": dom_rows, "ms_per_launch": dom_ms,
+                "launches_per_step": len(dom_blocks),
+                "algorithmic_bytes_per_launch": dom_rows * 8 * 8,
+                "all_leaf_launches": {"ms_per_step": leaf_ms, "flops_per_step": info["tsqr_leaf_flops"],
+                                      "tflops": info["tsqr_leaf_flops"] / (leaf_ms * 1e-3) / 1e12,
+                                      "launches_per_step": launches["tsqr_leaf"]},
+                "staged_ms_per_step": ms_staged, "largest_stage": dom}
     out = {
         "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak",

@@ -178,6 +178,15 @@ int figaro_plan_get_info(figaro_plan_t plan, figaro_plan_info* info);
 int figaro_stage_times(figaro_plan_t plan, double* ms, int64_t* counts, int32_t n);
 int figaro_reset_stage_times(figaro_plan_t plan);
 
+/* Per block of R0 (§7: for every relation in order, its tails block if it has data
+ * columns, then its generalized-tail block (inner relations) or the root block): the
+ * time of the block's TSQR leaf launches in milliseconds summed since the last reset
+ * (stage_timing = 1 only, else 0), its column count and its row count in the last
+ * call.  Any of the three host arrays may be NULL; at most `max` entries are written.
+ * A measurement aid (the paper has no counterpart).  Returns the number of blocks or a
+ * negative status.                                                                   */
+int figaro_block_times(figaro_plan_t plan, int32_t max, double* leaf_ms, int32_t* n_cols, int64_t* rows);
+
 /* Copy an intermediate array of relation `rel` from the last compute call to host
  * memory, for tests and diagnostics (a synchronous copy of at most `bytes` bytes).
  * Returns the number of bytes the array holds (>= 0) or a negative status.

@@ -78,6 +78,7 @@ def load(build_if_missing: bool = False):
         "figaro_plan_get_info": (C.c_int, [P, C.POINTER(figaro_plan_info)]),
         "figaro_stage_times": (C.c_int, [P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),
         "figaro_reset_stage_times": (C.c_int, [P]),
+        "figaro_block_times": (C.c_int, [P, C.c_int32, P, P, P]),
         "figaro_debug_read": (C.c_int64, [P, C.c_int32, C.c_int32, P, C.c_int64]),
         "figaro_svd_from_r_static": (C.c_int, [P, C.c_int64, C.c_int32, P, P, P]),
         "figaro_error_string": (C.c_char_p, [C.c_int]),
@@ -145,6 +146,17 @@ def figaro_stage_times(plan):
     cnt = (C.c_int64 * 8)()
     load().figaro_stage_times(plan, ms, cnt, 8)
     return {s: (ms[i], cnt[i]) for i, s in enumerate(STAGES)}
+
+
+def figaro_block_times(plan):
+    """[(leaf_ms, n_cols, rows)] per R0 block (see the header)."""
+    lib = load()
+    nb = lib.figaro_block_times(plan, 0, None, None, None)
+    if nb < 0:
+        check(-nb)
+    ms, nc, rows = (C.c_double * max(nb, 1))(), (C.c_int32 * max(nb, 1))(), (C.c_int64 * max(nb, 1))()
+    lib.figaro_block_times(plan, nb, C.cast(ms, C.c_void_p), C.cast(nc, C.c_void_p), C.cast(rows, C.c_void_p))
+    return [(ms[i], nc[i], rows[i]) for i in range(nb)]
 
 
 def figaro_reset_stage_times(plan):
@@ -241,6 +253,9 @@ class JoinPlan:
 
     def stage_times(self):
         return figaro_stage_times(self.handle)
+
+    def block_times(self):
+        return figaro_block_times(self.handle)
 
     def reset_stage_times(self):
         figaro_reset_stage_times(self.handle)

@@ -98,6 +98,8 @@ struct figaro_plan_s {
   bool graph_failed = false;
   int64_t graph_launches = 0;
   std::vector<cudaEvent_t> leaf_ev;    // stage timing: start/end of every block's leaf kernel
+  std::vector<double> block_leaf_ms;   // stage timing: leaf time per block since the last reset
+  std::vector<int64_t> block_rows;     // rows of every block in the last call
   double* Rtmp = nullptr;
   double* svdW = nullptr;
   double* svdV = nullptr;
@@ -872,14 +874,25 @@ static int finish(figaro_plan_s& P, int stages_used) {
       const int from = s == 6 ? 6 : s;           // stage 6 starts at its own event
       if (cudaEventElapsedTime(&ms, P.ev[from], P.ev[s + 1]) == cudaSuccess) P.stage_ms[s] += ms;
     }
+    P.block_leaf_ms.resize(P.blocks.size(), 0.0);
     for (size_t bi = 0; bi < P.blocks.size(); ++bi) {
       float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, P.leaf_ev[2 * bi], P.leaf_ev[2 * bi + 1]) == cudaSuccess) P.stage_ms[5] += ms;
+      if (cudaEventElapsedTime(&ms, P.leaf_ev[2 * bi], P.leaf_ev[2 * bi + 1]) == cudaSuccess) {
+        P.stage_ms[5] += ms;
+        P.block_leaf_ms[bi] += ms;
+      }
     }
   }
   // bookkeeping for figaro_plan_get_info: R0 rows and TSQR leaf flops of this call
   P.r0_rows = 0;
   P.leaf_flops = 0.0;
+  P.block_rows.assign(P.blocks.size(), 0);
+  for (size_t i = 0; i < P.nodes.size(); ++i) {
+    const Node& n = P.nodes[i];
+    const int64_t G = P.err_host[4 + 4 * i], Pg = P.err_host[4 + 4 * i + 1];
+    if (n.blk_tails >= 0) P.block_rows[n.blk_tails] = n.M - G;
+    if (n.blk_gen >= 0) P.block_rows[n.blk_gen] = n.root ? G : G - Pg;
+  }
   for (size_t i = 0; i < P.nodes.size(); ++i) {
     const Node& n = P.nodes[i];
     const int64_t G = P.err_host[4 + 4 * i], Pg = P.err_host[4 + 4 * i + 1];
@@ -1155,7 +1168,19 @@ int figaro_reset_stage_times(figaro_plan_t p) {
     p->stage_ms[s] = 0.0;
     p->stage_launch[s] = 0;
   }
+  for (auto& v : p->block_leaf_ms) v = 0.0;
   return FIGARO_OK;
+}
+
+int figaro_block_times(figaro_plan_t p, int32_t max, double* leaf_ms, int32_t* n_cols, int64_t* rows) {
+  if (!p || max < 0) return -FIGARO_ERR_INVALID_ARG;
+  const int nb = (int)p->blocks.size();
+  for (int b = 0; b < nb && b < max; ++b) {
+    if (leaf_ms) leaf_ms[b] = b < (int)p->block_leaf_ms.size() ? p->block_leaf_ms[b] : 0.0;
+    if (n_cols) n_cols[b] = p->blocks[b].n;
+    if (rows) rows[b] = b < (int)p->block_rows.size() ? p->block_rows[b] : 0;
+  }
+  return nb;
 }
 
 int64_t figaro_debug_read(figaro_plan_t p, int32_t rel, int32_t what, void* dst, int64_t bytes) {
