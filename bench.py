@@ -225,6 +225,16 @@ def run_figaro(args):
     mx_stages = {k: v[0] / args.steps for k, v in pmxs.stage_times().items()}
     pmxs.close()
 
+    # --- mixed path with the CholeskyQR2-style refinement
+    pmr = binding.JoinPlan(dev_inputs, db.parent, precision=binding.FIGARO_PREC_MIXED_REFINED, stream=stream)
+    pmr._R = torch.empty(db.n_cols, db.n_cols, dtype=torch.float64, device="cuda")
+    msmr = max_over_ranks(time_steps(pmr, torch, args.steps, args.warmup, barrier))
+    Rmr = pmr._R.cpu().numpy()
+    refined = int(pmr.info()["refined"])
+    pmr.close()
+    err_mr = float(np.linalg.norm(Rmr.T @ Rmr - G64) / np.linalg.norm(G64))
+    err_mr_r = float(np.linalg.norm(Rmr - R64) / np.linalg.norm(R64))
+
     # --- end to end through the C ABI with pinned host buffers
     host_inputs = make_inputs(db, torch, "cpu")
     ph = binding.JoinPlan(host_inputs, db.parent, mem=binding.FIGARO_MEM_HOST, stream=stream)
@@ -279,6 +289,11 @@ def run_figaro(args):
         "gbs": gbs, "hbm_frac": gbs / hbm, "hbm_peak_gbs": hbm, "hbm_peak_kind": hbm_kind,
         "mixed": {"ms_per_step": msmx, "value": cells * world / (msmx * 1e-3), "speedup_vs_fp64": ms64 / msmx,
                   "rel_err_RtR_vs_fp64_path": err_mx, "stages_ms_per_step": mx_stages,
+                  "refined": {"ms_per_step": msmr, "value": cells * world / (msmr * 1e-3),
+                              "speedup_vs_fp64": ms64 / msmr, "refinement_applied": refined,
+                              "rel_err_RtR_vs_fp64_path": err_mr, "rel_err_R_vs_fp64_path": err_mr_r,
+                              "dtype": "mixed path + one CholeskyQR2-style correction with A^T A in "
+                                       "double-float"},
                   "dtype": "double-float head/tail sums, f32 tails and TSQR leaf/tree, f64 counts, join, final QR"},
         "stages_ms_per_step": per_stage,
         "stage_note": "from a stage-timed plan with serialised TSQR chains; tsqr_tree = whole TSQR section, tsqr_leaf = its leaf launches",

@@ -54,7 +54,7 @@ enum figaro_status {
 
 enum { FIGARO_KEY_I64 = 0, FIGARO_KEY_I32 = 1 };
 enum { FIGARO_COL_MAJOR = 0, FIGARO_ROW_MAJOR = 1 };
-enum { FIGARO_PREC_FP64 = 0, FIGARO_PREC_MIXED = 1 };
+enum { FIGARO_PREC_FP64 = 0, FIGARO_PREC_MIXED = 1, FIGARO_PREC_MIXED_REFINED = 2 };
 enum { FIGARO_MEM_DEVICE = 0, FIGARO_MEM_HOST = 1 };
 
 /* One relation S_i (§2 "Relations and Joins").
@@ -95,6 +95,13 @@ typedef struct figaro_join_tree {
  *                    (two floats, about 46 bits) with float32 tail rows; the TSQR leaf
  *                    tiles and tree levels of every R0 block in float32; the final QR
  *                    of the stacked block triangles, R, SVD and PCA in float64.
+ *                    FIGARO_PREC_MIXED_REFINED: the mixed path followed by one
+ *                    CholeskyQR2-style correction (the paper has none): A^T A = R0^T R0
+ *                    (Theorem of §6) is accumulated in double-float arithmetic from the
+ *                    unrounded tail rows and the float64 blocks, and R = C R~ with
+ *                    C = chol(R~^-T A^T A R~^-1) for the mixed R~.  When that Cholesky
+ *                    factorisation breaks down (A too ill-conditioned for float32 TSQR),
+ *                    R~ is returned as it is and figaro_plan_get_info reports refined = 0.
  *   presorted        1: every relation is already sorted by its key (the order §5
  *                    assumes: attributes shared with the parent first, then the rest,
  *                    each part in ascending attribute id, values ascending); the sort
@@ -125,6 +132,8 @@ typedef struct figaro_plan_info {
   int64_t r0_rows;             /* rows of R0 after the last call (<= sum_i M_i)       */
   int64_t launches;            /* kernels launched by the last compute call           */
   double tsqr_leaf_flops;      /* algorithmic flops of the TSQR leaf tiles, last call */
+  int32_t refined;             /* FIGARO_PREC_MIXED_REFINED: 1 if the last call refined R */
+  int32_t reserved;
 } figaro_plan_info;
 
 /* Fill *opt with the defaults (FP64, not presorted, reduce, device memory, no timing). */

@@ -17,7 +17,7 @@ from . import build_lib
 FIGARO_OK = 0
 FIGARO_KEY_I64, FIGARO_KEY_I32 = 0, 1
 FIGARO_COL_MAJOR, FIGARO_ROW_MAJOR = 0, 1
-FIGARO_PREC_FP64, FIGARO_PREC_MIXED = 0, 1
+FIGARO_PREC_FP64, FIGARO_PREC_MIXED, FIGARO_PREC_MIXED_REFINED = 0, 1, 2
 FIGARO_MEM_DEVICE, FIGARO_MEM_HOST = 0, 1
 DBG = {"sizes": 0, "perm": 1, "group_off": 2, "counts": 3, "pcounts": 4, "tails": 5, "heads": 6,
        "gen_tails": 7, "data": 8, "root_rows": 9}
@@ -44,7 +44,8 @@ class figaro_options(C.Structure):
 class figaro_plan_info(C.Structure):
     _fields_ = [("n_rel", C.c_int32), ("n_cols", C.c_int32), ("input_cells", C.c_int64),
                 ("input_bytes", C.c_int64), ("workspace_bytes", C.c_int64), ("r0_rows", C.c_int64),
-                ("launches", C.c_int64), ("tsqr_leaf_flops", C.c_double)]
+                ("launches", C.c_int64), ("tsqr_leaf_flops", C.c_double), ("refined", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class FigaroError(RuntimeError):

@@ -113,6 +113,13 @@ struct figaro_plan_s {
   int64_t input_cells = 0, input_bytes = 0;
   double leaf_flops = 0.0;
   int64_t r0_rows = 0;
+  // refinement of the mixed R (FIGARO_PREC_MIXED_REFINED)
+  std::vector<double*> gram_partial;   // per block: per-CTA partial Gram matrices
+  std::vector<const float*> block_lo32; // per block: low floats of its rows (tails blocks)
+  double* gram = nullptr;              // A^T A (N x N)
+  double* refine_w = nullptr;          // two N x N work arrays
+  int* refine_ok = nullptr;            // device: 1 when the last refinement was applied
+  int refined = 0;
 };
 
 namespace fig {
@@ -138,7 +145,8 @@ static int bits_for(unsigned long long range) {
 
 // Lays out every device buffer of the plan; with a.base == nullptr only measures.
 static void layout(figaro_plan_s& P, Arena& a) {
-  const bool mixed = P.opt.precision == FIGARO_PREC_MIXED;
+  const bool mixed = P.opt.precision != FIGARO_PREC_FP64;
+  const bool refine = P.opt.precision == FIGARO_PREC_MIXED_REFINED;
   int64_t maxM = 1;
   for (auto& n : P.nodes) maxM = std::max(maxM, n.M);
   P.err_dev = a.take<int>(4);
@@ -188,6 +196,7 @@ static void layout(figaro_plan_s& P, Arena& a) {
     b.heads = a.take<double>(M * std::max(n.N, 1));
     b.tails = a.take<double>(M * std::max(n.N, 1));
     b.tails32 = mixed ? a.take<float>(M * std::max(n.N, 1)) : nullptr;
+    b.tails32lo = refine ? a.take<float>(M * std::max(n.N, 1)) : nullptr;
     if (!n.leaf && !n.root) {
       b.data2 = a.take<double>(M * n.N_sub);
       b.gtails = a.take<double>(M * n.N_sub);
@@ -220,6 +229,13 @@ static void layout(figaro_plan_s& P, Arena& a) {
   P.stack_blk.tri[1] = a.take<double>(tsqr_tri_elems(P.stack_blk));
   const int64_t NN = (int64_t)P.N * P.N;
   P.Rtmp = a.take<double>(NN);
+  P.gram_partial.assign(P.blocks.size(), nullptr);
+  if (refine) {
+    for (size_t bi = 0; bi < P.blocks.size(); ++bi) P.gram_partial[bi] = a.take<double>(gram_partial_elems(P.blocks[bi]));
+    P.gram = a.take<double>(NN);
+    P.refine_w = a.take<double>(2 * NN);
+    P.refine_ok = a.take<int>(1);
+  }
   P.svdW = a.take<double>(NN);
   P.svdV = a.take<double>(NN);
   P.sig = a.take<double>(P.N);
@@ -465,7 +481,7 @@ static void make_links(figaro_plan_s& P) {
 }
 
 static void make_blocks(figaro_plan_s& P) {
-  const bool mixed = P.opt.precision == FIGARO_PREC_MIXED;
+  const bool mixed = P.opt.precision != FIGARO_PREC_FP64;
   P.blocks.clear();
   P.stack_rows = 0;
   for (auto& n : P.nodes) {
@@ -519,8 +535,10 @@ static void make_blocks(figaro_plan_s& P) {
 // block pointers that depend on the arena
 static void bind_blocks(figaro_plan_s& P) {
   size_t bi = 0;
+  P.block_lo32.assign(P.blocks.size(), nullptr);
   for (auto& n : P.nodes) {
     if (n.N > 0) {
+      P.block_lo32[bi] = n.b.tails32lo;
       P.blocks[bi].ptr = n.b.tails;
       P.blocks[bi].ptr32 = n.b.tails32;
       P.blocks[bi].ld = n.M;
@@ -591,7 +609,8 @@ struct StageClock {
 // chains last, so that each stage's event times cover only its own kernels.
 static int enqueue_r(figaro_plan_s& P, double* R, int64_t ldr) {
   cudaStream_t st = P.st;
-  const bool mixed = P.opt.precision == FIGARO_PREC_MIXED;
+  const bool mixed = P.opt.precision != FIGARO_PREC_FP64;
+  const bool refine = P.opt.precision == FIGARO_PREC_MIXED_REFINED;
   const bool serial = P.opt.stage_timing != 0;
   const bool host = P.opt.mem == FIGARO_MEM_HOST;
   const int r = (int)P.nodes.size();
@@ -600,6 +619,7 @@ static int enqueue_r(figaro_plan_s& P, double* R, int64_t ldr) {
   auto rec = [&](cudaEvent_t e, cudaStream_t s) { return serial ? cudaSuccess : cudaEventRecord(e, s); };
   auto wait = [&](cudaStream_t s, cudaEvent_t e) { return serial ? cudaSuccess : cudaStreamWaitEvent(s, e, 0); };
   FIG_CUDA(cudaMemsetAsync(P.err_dev, 0, sizeof(int), st));
+  if (refine) FIG_CUDA(cudaMemsetAsync(P.gram, 0, sizeof(double) * P.N * P.N, st));
   FIG_CUDA(rec(P.fork, st));
   if (host) {
     cudaStream_t cs = serial ? st : P.copy_st;
@@ -630,6 +650,7 @@ static int enqueue_r(figaro_plan_s& P, double* R, int64_t ldr) {
     P.stage_launch[5] += P.launches - l0;
     if (serial) FIG_CUDA(cudaEventRecord(P.leaf_ev[2 * bi + 1], s));
     tsqr_reduce(P.blocks[bi], mixed, s, &P.launches);
+    if (refine) gram_block(P.blocks[bi], P.block_lo32[bi], P.gram_partial[bi], s, &P.launches);
     FIG_CUDA(rec(P.side_done[bi], s));
     return FIGARO_OK;
   };
@@ -741,6 +762,7 @@ static int enqueue_r(figaro_plan_s& P, double* R, int64_t ldr) {
     lp.beta_len = P.beta_len;
     lp.tails = n.b.tails;
     lp.tails32 = mixed ? n.b.tails32 : nullptr;
+    lp.tails32lo = refine ? n.b.tails32lo : nullptr;
     lp.ldt = n.M;
     lp.heads = n.b.heads;
     lp.ldh = n.M;
@@ -813,7 +835,11 @@ static int enqueue_r(figaro_plan_s& P, double* R, int64_t ldr) {
       FIG_CUDA(cudaStreamWaitEvent(st, P.side_done[bi], 0));
     }
   }
+  if (refine)
+    for (size_t bi = 0; bi < P.blocks.size(); ++bi) gram_add(P.blocks[bi], P.gram_partial[bi], P.gram, P.N, st, &P.launches);
   tsqr_final(P.blocks_dev, (int)P.blocks.size(), P.stack_blk, R, ldr, st, &P.launches);
+  if (refine)
+    refine_r(R, ldr, P.gram, P.N, P.refine_w, P.refine_w + (int64_t)P.N * P.N, P.refine_ok, st, &P.launches);
   clk.stop();
   FIG_CUDA(cudaGetLastError());
   return FIGARO_OK;
@@ -862,6 +888,7 @@ static int run_r(figaro_plan_s& P, double* R, int64_t ldr) {
 
 static int finish(figaro_plan_s& P, int stages_used) {
   FIG_CUDA(cudaMemcpyAsync(P.err_host, P.err_dev, sizeof(int), cudaMemcpyDeviceToHost, P.st));
+  if (P.refine_ok) FIG_CUDA(cudaMemcpyAsync(P.err_host + 1, P.refine_ok, sizeof(int), cudaMemcpyDeviceToHost, P.st));
   for (size_t i = 0; i < P.nodes.size(); ++i)
     FIG_CUDA(cudaMemcpyAsync(P.err_host + 4 + 4 * i, P.nodes[i].b.sizes, 4 * sizeof(int32_t),
                              cudaMemcpyDeviceToHost, P.st));
@@ -886,6 +913,7 @@ static int finish(figaro_plan_s& P, int stages_used) {
   // bookkeeping for figaro_plan_get_info: R0 rows and TSQR leaf flops of this call
   P.r0_rows = 0;
   P.leaf_flops = 0.0;
+  P.refined = P.refine_ok ? P.err_host[1] : 0;
   P.block_rows.assign(P.blocks.size(), 0);
   for (size_t i = 0; i < P.nodes.size(); ++i) {
     const Node& n = P.nodes[i];
@@ -974,7 +1002,8 @@ int figaro_plan(const figaro_join_tree* tree, const figaro_options* opt, void* s
   auto* P = new (std::nothrow) figaro_plan_s();
   if (!P) return fail(FIGARO_ERR_NOMEM, "host allocation");
   if (opt) P->opt = *opt; else figaro_default_options(&P->opt);
-  if (P->opt.precision != FIGARO_PREC_FP64 && P->opt.precision != FIGARO_PREC_MIXED) {
+  if (P->opt.precision != FIGARO_PREC_FP64 && P->opt.precision != FIGARO_PREC_MIXED &&
+      P->opt.precision != FIGARO_PREC_MIXED_REFINED) {
     delete P;
     return fail(FIGARO_ERR_INVALID_ARG, "precision");
   }
@@ -989,6 +1018,7 @@ int figaro_plan(const figaro_join_tree* tree, const figaro_options* opt, void* s
     cudaError_t e = keys_set_attributes();
     if (e == cudaSuccess) e = tsqr_set_attributes();
     if (e == cudaSuccess) e = svd_set_attributes();
+    if (e == cudaSuccess) e = refine_set_attributes();
     if (e != cudaSuccess) {
       delete P;
       return fail(FIGARO_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
@@ -1150,6 +1180,8 @@ int figaro_plan_get_info(figaro_plan_t p, figaro_plan_info* info) {
   info->r0_rows = p->r0_rows;
   info->launches = p->launches;
   info->tsqr_leaf_flops = p->leaf_flops;
+  info->refined = p->refined;
+  info->reserved = 0;
   return FIGARO_OK;
 }
 

@@ -307,6 +307,7 @@ __global__ void __launch_bounds__(256) k_leaf_agg_mx(LeafParams p) {
   }
 }
 
+template <bool LO>
 __global__ void __launch_bounds__(256, 2) k_leaf_emit_mx(LeafParams p) {
   const int lane = threadIdx.x & 31;
   const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -314,13 +315,14 @@ __global__ void __launch_bounds__(256, 2) k_leaf_emit_mx(LeafParams p) {
   for (int64_t t = wid; t < p.n_tiles; t += nwarps) {
     const int64_t e0 = t * kHtTile + (int64_t)lane * kHtItems;
     LeafRow rw[kHtItems];
-    float gam[kHtItems];
+    dfl gam[kHtItems];                    // sqrt(Phi_circ) beta_p (the low part only when refining)
     dfl pos[kHtItems];
 #pragma unroll
     for (int i = 0; i < kHtItems; ++i) {
       rw[i] = leaf_row(p, e0 + i);
       const bool tail = rw[i].ok && rw[i].pos > 0;
-      gam[i] = tail ? (float)(p.sq_phic[rw[i].g] * p.beta[rw[i].pos].x) : 0.0f;
+      const double g = tail ? p.sq_phic[rw[i].g] * p.beta[rw[i].pos].x : 0.0;
+      gam[i] = LO ? df_from_double(g) : dfl{(float)g, 0.0f};
       pos[i] = df_from_count(rw[i].pos);
     }
     for (int c = 0; c < p.N; ++c) {
@@ -338,7 +340,14 @@ __global__ void __launch_bounds__(256, 2) k_leaf_emit_mx(LeafParams p) {
         if (rw[i].pos == 0) run = dfl{0.0f, 0.0f};
         if (rw[i].pos > 0) {
           const dfl d = df_add(df_mul(x, pos[i]), df_neg(run));
-          tcol[e0 + i - rw[i].g - 1] = gam[i] * (d.hi + d.lo);
+          const int64_t row = e0 + i - rw[i].g - 1;
+          if (LO) {                        // the double-float tail, kept for the refinement's Gram
+            const dfl tt = df_mul(d, gam[i]);
+            tcol[row] = tt.hi;
+            p.tails32lo[(int64_t)c * p.ldt + row] = tt.lo;
+          } else {
+            tcol[row] = gam[i].hi * (d.hi + d.lo);
+          }
         }
         run = df_add(run, x);
         // the pair's bits, combined and scaled by heads_finish (a conversion here would be
@@ -379,7 +388,8 @@ void leaf_heads_tails(const LeafParams& p, const int32_t* sizes, cudaStream_t st
   if (p.tails32) k_leaf_agg_mx<<<g, 256, 0, st>>>(p);
   else k_leaf_agg<<<g, 256, 0, st>>>(p);
   k_tile_carry<<<p.N, kCarryThreads, 0, st>>>(p.tflag, p.tsum, p.tcarry, p.n_tiles, nullptr);
-  if (p.tails32) k_leaf_emit_mx<<<g, 256, 0, st>>>(p);
+  if (p.tails32 && p.tails32lo) k_leaf_emit_mx<true><<<g, 256, 0, st>>>(p);
+  else if (p.tails32) k_leaf_emit_mx<false><<<g, 256, 0, st>>>(p);
   else k_leaf_emit<<<g, 256, 0, st>>>(p);
   k_heads_finish<<<grid_for(p.M * (int64_t)p.N, 256, 152 * 8), 256, 0, st>>>(p, sizes, p.tails32 != nullptr);
   *launches += 4;

@@ -53,6 +53,7 @@ struct NodeBuf {
   double* heads;        // [M x N_i] col-major, ld M
   double* tails;        // [M x N_i] col-major, ld M  (rows M - G used)
   float* tails32;       // optional float copy for the mixed TSQR
+  float* tails32lo;     // refined mixed path: the low float of each double-float tail
   double* data2;        // [M x N_sub] col-major: generalized heads for the parent
   double* gtails;       // [M x N_sub] col-major: generalized tails
   double* rootrows;     // [M x N] col-major (root only)
@@ -145,6 +146,7 @@ struct LeafParams {
   double* tails;
   int64_t ldt;
   float* tails32;            // mixed precision: float tails (leading dimension ldt) instead of tails
+  float* tails32lo;          // with tails32, optional: the low parts (tail = tails32 + tails32lo)
   double* heads;
   int64_t ldh;
   uint8_t* tflag;
@@ -227,5 +229,13 @@ cudaError_t svd_set_attributes();
 void jacobi_svd(const double* R, int64_t ldr, int N, double* W, double* V, double* sigma,
                 double* Vout, int* err, cudaStream_t st, int64_t* launches);
 void square_values(const double* s, double* out, int k, cudaStream_t st, int64_t* launches);
+
+// ------------------------------------------------------------------ refine.cu
+cudaError_t refine_set_attributes();
+int64_t gram_partial_elems(const TsqrBlock& b);
+void gram_block(const TsqrBlock& b, const float* lo32, double* partial, cudaStream_t st, int64_t* launches);
+void gram_add(const TsqrBlock& b, const double* partial, double* G, int N, cudaStream_t st, int64_t* launches);
+void refine_r(double* R, int64_t ldr, const double* G, int N, double* W1, double* W2, int* ok, cudaStream_t st,
+              int64_t* launches);
 
 }  // namespace fig

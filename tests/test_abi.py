@@ -107,4 +107,4 @@ def test_struct_layouts_match_header():
     assert C.sizeof(binding.figaro_relation) == 56
     assert C.sizeof(binding.figaro_join_tree) == 24
     assert C.sizeof(binding.figaro_options) == 64
-    assert C.sizeof(binding.figaro_plan_info) == 56
+    assert C.sizeof(binding.figaro_plan_info) == 64

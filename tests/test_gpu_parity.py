@@ -360,3 +360,44 @@ def test_mixed_heads_are_double_float_accurate():
         h = p.debug(i, "heads", np.float64).reshape(rel.n_data, -1).T
         close(h, heads_o, tol=1e-12)
     p.close()
+
+
+# ------------------------------------------------------------------ refined mixed path
+
+REFINED_CASES = {
+    "two_relation": lambda: synth.two_relation(seed=1),
+    "path3": lambda: synth.path3(rows=30_000, keys=500),
+    "star": lambda: synth.star(fact_rows=20_000, dim_rows=2000, keys=500, n_cols=4),
+    "snowflake_scaled": lambda: synth.snowflake(f_rows=50_000, d1_rows=5000, d2_rows=4000, d3_rows=300,
+                                                n_cols=6),
+    "random_tree_dangling": lambda: synth.random_tree_db(30, n_rel=6, domain=4, dangling=True, rows_hi=40),
+}
+
+
+@pytest.mark.parametrize("name", sorted(REFINED_CASES))
+def test_mixed_refined_reaches_fp64_tolerance(name):
+    """One CholeskyQR2-style correction with A^T A accumulated in double-float brings the
+    float32-TSQR R to the FP64 tolerance."""
+    from paper_2204_00525_gb300 import binding
+    db = REFINED_CASES[name]()
+    R_o = ofg.figaro_r(db)
+    p = plan_for(db, precision=binding.FIGARO_PREC_MIXED_REFINED)
+    R = p.qr_r().cpu().numpy()
+    assert p.info()["refined"] == 1
+    p.close()
+    assert rel_err(R, R_o) < TOL_R
+    assert np.all(np.diag(R) >= 0) and np.array_equal(np.tril(R, -1), np.zeros_like(R))
+
+
+def test_full_size_path_join_refined(path3_full):
+    from paper_2204_00525_gb300 import binding
+    db, G = path3_full
+    p = plan_for(db, precision=binding.FIGARO_PREC_MIXED_REFINED)
+    R = p.qr_r().cpu().numpy()
+    assert p.info()["refined"] == 1
+    s, _ = p.svd()
+    p.close()
+    assert rel_err(R.T @ R, G) < TOL_R
+    assert rel_err(R, np.linalg.cholesky(G).T) < 1e-9
+    lam = np.linalg.eigvalsh(G)[::-1]
+    assert np.max(np.abs(s.cpu().numpy() ** 2 - lam)) / lam[0] < 1e-10
