@@ -22,6 +22,8 @@ aggregates).  Each function cites the passage of the paper it follows:
   gram.py         A^T A by factorized aggregation over the join tree (independent of
                   Alg. 3/4), used to check R^T R = A^T A at any size
   spectral.py     §8.2-8.3: SVD and PCA of A through the SVD of R
+  grad.py         gradients of a loss on R with respect to the relations' data columns
+                  (matrix calculus of the QR factor; join sums by message passing)
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test in
 ``tests/test_oracle_*.py`` against closed forms, brute force, library routines or
