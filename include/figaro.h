@@ -49,7 +49,8 @@ enum figaro_status {
   FIGARO_ERR_CUDA = 7,          /* a CUDA runtime call failed (see figaro_last_error)     */
   FIGARO_ERR_KEY_RANGE = 8,     /* a key value lies outside the range seen by figaro_plan */
   FIGARO_ERR_NOT_SORTED = 9,    /* presorted was set but a relation is not sorted         */
-  FIGARO_ERR_UNSUPPORTED = 10   /* a size limit of this build (see below) is exceeded     */
+  FIGARO_ERR_UNSUPPORTED = 10,  /* a size limit of this build (see below) is exceeded     */
+  FIGARO_ERR_SINGULAR = 11      /* figaro_backward: R has a zero diagonal entry           */
 };
 
 enum { FIGARO_KEY_I64 = 0, FIGARO_KEY_I32 = 1 };
@@ -110,14 +111,16 @@ typedef struct figaro_join_tree {
  *                    (the paper assumes fully reduced input, §2); 0 (default): such
  *                    tuples are given weight 0, which is exact since they are not in A.
  *   mem              FIGARO_MEM_DEVICE or FIGARO_MEM_HOST (see the conventions).
- *   stage_timing     1: time every stage with CUDA events (figaro_stage_times).      */
+ *   stage_timing     1: time every stage with CUDA events (figaro_stage_times).
+ *   gradients        1: also hold the workspace of figaro_backward (device memory only). */
 typedef struct figaro_options {
   int32_t precision;
   int32_t presorted;
   int32_t require_reduced;
   int32_t mem;
   int32_t stage_timing;
-  int32_t reserved[11];
+  int32_t gradients;
+  int32_t reserved[10];
 } figaro_options;
 
 typedef struct figaro_plan_s* figaro_plan_t;
@@ -169,6 +172,25 @@ int figaro_svd(figaro_plan_t plan, double* sigma, double* V, double* R);
  * right singular vector of the j-th largest singular value), eigvals[k] = sigma^2.
  * 1 <= k <= N. */
 int figaro_pca(figaro_plan_t plan, int32_t k, double* components, double* eigvals);
+
+/* Gradient of a loss L(R) with respect to every relation's data columns, at the data of
+ * the last figaro_qr_r / figaro_svd / figaro_pca call on this plan (made with
+ * gradients = 1 and mem = FIGARO_MEM_DEVICE).  The paper does not differentiate R; with
+ * Rbar = dL/dR (only its upper triangle matters), R of full column rank, and
+ * W = R^-1 copyltu(R Rbar^T) R^-T (copyltu mirrors the lower triangle), dL/dA = A W for
+ * the join matrix A, and the gradient for tuple t of relation k is
+ * m(t)^T W[:, Y_k], m(t) the sum of the join rows that contain t (Phi_circ(t) y_t on Y_k,
+ * sums from messages over the join tree, counted with Alg. 3's aggregates, elsewhere).
+ *   R      device, N x N row-major (ldr >= N): the R that call returned.
+ *   Rbar   device, N x N row-major (ldb >= N).
+ *   grads  host array of n_rel device pointers: relation i's gradient, column-major
+ *          M_i x N_i with leading dimension ldg[i] >= M_i, in the input row order
+ *          (NULL for a relation without data columns).
+ * Errors: FIGARO_ERR_SINGULAR (a zero diagonal entry of R), FIGARO_ERR_UNSUPPORTED (plan
+ * without gradients or in host-memory mode).  Sums are formed with atomics: results are
+ * accurate to rounding but not bitwise reproducible.  Synchronous.                     */
+int figaro_backward(figaro_plan_t plan, const double* R, int64_t ldr, const double* Rbar, int64_t ldb,
+                    double* const* grads, const int64_t* ldg);
 
 /* Release the plan's workspace (waits for its stream).  NULL is accepted. */
 int figaro_plan_destroy(figaro_plan_t plan);

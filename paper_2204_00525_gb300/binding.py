@@ -38,7 +38,8 @@ class figaro_join_tree(C.Structure):
 
 class figaro_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("presorted", C.c_int32), ("require_reduced", C.c_int32),
-                ("mem", C.c_int32), ("stage_timing", C.c_int32), ("reserved", C.c_int32 * 11)]
+                ("mem", C.c_int32), ("stage_timing", C.c_int32), ("gradients", C.c_int32),
+                ("reserved", C.c_int32 * 10)]
 
 
 class figaro_plan_info(C.Structure):
@@ -82,6 +83,7 @@ def load(build_if_missing: bool = False):
         "figaro_block_times": (C.c_int, [P, C.c_int32, P, P, P]),
         "figaro_debug_read": (C.c_int64, [P, C.c_int32, C.c_int32, P, C.c_int64]),
         "figaro_svd_from_r_static": (C.c_int, [P, C.c_int64, C.c_int32, P, P, P]),
+        "figaro_backward": (C.c_int, [P, P, C.c_int64, P, C.c_int64, P, P]),
         "figaro_error_string": (C.c_char_p, [C.c_int]),
         "figaro_last_error": (C.c_char_p, []),
     }
@@ -130,6 +132,14 @@ def figaro_pca(plan, k: int, comp_ptr: int, eig_ptr: int):
 def figaro_svd_from_r_static(R_ptr: int, ldr: int, n: int, sigma_ptr: int, V_ptr: int, stream: int):
     return check(load().figaro_svd_from_r_static(C.c_void_p(R_ptr), ldr, n, C.c_void_p(sigma_ptr),
                                                  C.c_void_p(V_ptr), C.c_void_p(stream)))
+
+
+def figaro_backward(plan, R_ptr: int, ldr: int, Rbar_ptr: int, ldb: int, grad_ptrs, ldgs):
+    n = len(grad_ptrs)
+    ptrs = (C.c_void_p * max(n, 1))(*[C.c_void_p(p) if p else None for p in grad_ptrs])
+    lds = (C.c_int64 * max(n, 1))(*ldgs)
+    return check(load().figaro_backward(plan, C.c_void_p(R_ptr), ldr, C.c_void_p(Rbar_ptr), ldb,
+                                        C.cast(ptrs, C.c_void_p), C.cast(lds, C.c_void_p)))
 
 
 def figaro_plan_destroy(plan):
@@ -188,9 +198,11 @@ class JoinPlan:
     asynchronous copies, with ``mem=FIGARO_MEM_HOST``)."""
 
     def __init__(self, relations, parent, precision=FIGARO_PREC_FP64, presorted=False,
-                 require_reduced=False, mem=FIGARO_MEM_DEVICE, stage_timing=False, stream=None):
+                 require_reduced=False, mem=FIGARO_MEM_DEVICE, stage_timing=False, stream=None,
+                 gradients=False):
         import torch
         self._keep = []
+        self._data = []
         n = len(relations)
         rels = (figaro_relation * n)()
         self._arrays = []
@@ -210,6 +222,7 @@ class JoinPlan:
             cols = (C.c_void_p * max(len(keys), 1))(*[k.data_ptr() for k in keys])
             self._arrays += [attrs, cols]
             self._keep += keys + [data]
+            self._data.append(data)
             rels[i] = figaro_relation(m, len(keys), kt, attrs, cols, nd, layout, ld,
                                       data.data_ptr() if nd > 0 else None)
         par = (C.c_int32 * n)(*parent)
@@ -221,6 +234,7 @@ class JoinPlan:
         opt.require_reduced = int(require_reduced)
         opt.mem = mem
         opt.stage_timing = int(stage_timing)
+        opt.gradients = int(gradients)
         self.mem = mem
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.handle = figaro_plan(tree, opt, self.stream.cuda_stream)
@@ -248,6 +262,27 @@ class JoinPlan:
         comp, ev = self._out(self.n_cols, k), self._out(k)
         figaro_pca(self.handle, k, comp.data_ptr(), ev.data_ptr())
         return comp, ev
+
+    def backward(self, R, Rbar):
+        """Gradients of a loss with dL/dR = Rbar at the last call's data: one
+        column-major (M_i, N_i) float64 tensor per relation (None without data columns)."""
+        import torch
+        R = R.contiguous()
+        Rbar = Rbar.to(device=R.device, dtype=torch.float64).contiguous()
+        grads, ptrs, lds = [], [], []
+        for d in self._data:
+            m, nd = d.shape
+            if nd == 0:
+                grads.append(None)
+                ptrs.append(0)
+                lds.append(max(m, 1))
+                continue
+            g = torch.empty(nd, m, dtype=torch.float64, device=R.device).t()   # column-major
+            grads.append(g)
+            ptrs.append(g.data_ptr())
+            lds.append(max(m, 1))
+        figaro_backward(self.handle, R.data_ptr(), R.stride(0), Rbar.data_ptr(), Rbar.stride(0), ptrs, lds)
+        return grads
 
     def info(self):
         return figaro_plan_get_info(self.handle)
@@ -298,3 +333,34 @@ def plan_from_db(db, device="cuda", precision=FIGARO_PREC_FP64, col_major=True, 
         rels.append({"keys": keys, "key_attrs": list(r.key_attrs), "data": data})
     return JoinPlan(rels, list(db.parent), precision=precision,
                     mem=FIGARO_MEM_HOST if host else FIGARO_MEM_DEVICE, **kw)
+
+
+class FigaroR:
+    """R of the join as a differentiable function of the relations' data tensors.
+
+    ``FigaroR(plan)(*datas)`` runs figaro_qr_r (the plan must have been made over exactly
+    these tensors, with gradients=True) and returns R; its backward calls figaro_backward
+    with the incoming dL/dR."""
+
+    def __init__(self, plan):
+        import torch
+
+        class _Fn(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, *datas):
+                R = plan.qr_r()
+                ctx.save_for_backward(R)
+                return R
+
+            @staticmethod
+            def backward(ctx, Rbar):
+                (R,) = ctx.saved_tensors
+                grads = plan.backward(R, Rbar)
+                return tuple(grads)
+
+        self._fn = _Fn
+        self.plan = plan
+
+    def __call__(self, *datas):
+        return self._fn.apply(*datas)
+

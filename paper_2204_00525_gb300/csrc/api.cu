@@ -61,6 +61,13 @@ struct Node {
   int32_t* radix_hist = nullptr;        // per relation: the sorts run concurrently
   int32_t* radix_tmp = nullptr;
   int blk_tails = -1, blk_gen = -1;     // R0 blocks fed by this relation (index into blocks)
+  // gradients (options.gradients): messages over the join tree, per-group shares
+  int64_t pbound = 1;                   // bound on the number of X_p groups
+  double* g_up = nullptr;               // [N][pbound]
+  double* g_dn = nullptr;               // [N][pbound]
+  double* g_phi = nullptr;              // [N_i][M]
+  uint8_t* g_colkind = nullptr;         // [N]
+  std::vector<uint8_t> colkind;
 };
 
 }  // namespace fig
@@ -120,6 +127,7 @@ struct figaro_plan_s {
   double* refine_w = nullptr;          // two N x N work arrays
   int* refine_ok = nullptr;            // device: 1 when the last refinement was applied
   int refined = 0;
+  double* grad_w = nullptr;            // gradients: W and two N x N work arrays
 };
 
 namespace fig {
@@ -210,6 +218,12 @@ static void layout(figaro_plan_s& P, Arena& a) {
     b.lflag = a.take<uint8_t>(n.n_tiles * wide * 32);
     b.lsum = a.take<double>(n.n_tiles * wide * 32);
     b.coldesc = a.take<int2>(std::max(n.N_sub, 1));
+    if (P.opt.gradients) {
+      n.g_up = a.take<double>((int64_t)P.N * n.pbound);
+      n.g_dn = a.take<double>((int64_t)P.N * n.pbound);
+      n.g_phi = a.take<double>(M * std::max(n.N, 1));
+      n.g_colkind = a.take<uint8_t>(P.N);
+    }
   }
   for (auto& blk : P.blocks) {
     blk.tri[0] = a.take<double>(tsqr_tri_elems(blk));
@@ -229,6 +243,7 @@ static void layout(figaro_plan_s& P, Arena& a) {
   P.stack_blk.tri[1] = a.take<double>(tsqr_tri_elems(P.stack_blk));
   const int64_t NN = (int64_t)P.N * P.N;
   P.Rtmp = a.take<double>(NN);
+  if (P.opt.gradients) P.grad_w = a.take<double>(3 * NN);
   P.gram_partial.assign(P.blocks.size(), nullptr);
   if (refine) {
     for (size_t bi = 0; bi < P.blocks.size(); ++bi) P.gram_partial[bi] = a.take<double>(gram_partial_elems(P.blocks[bi]));
@@ -364,6 +379,11 @@ static int build(figaro_plan_s& P, const figaro_join_tree* tree) {
         }
       }
     }
+    // every global column: 0 own, 1 + c in child c's subtree, 255 outside the subtree
+    n.colkind.assign(P.N, 255);
+    for (int c = 0; c < n.N; ++c) n.colkind[n.col_off + c] = 0;
+    for (int jj = 0; jj < (int)n.children.size(); ++jj)
+      for (int gc : P.nodes[n.children[jj]].sub_cols) n.colkind[gc] = (uint8_t)(1 + jj);
   }
   return FIGARO_OK;
 }
@@ -435,6 +455,9 @@ static int scan_key_ranges(figaro_plan_s& P) {
     n.bits = total;
     n.rest_bits = 0;
     for (int a : rest) n.rest_bits += P.abits[a];
+    const int xp_bits = total - n.rest_bits;   // distinct X_p values <= 2^xp_bits
+    n.pbound = n.root ? 1 : (xp_bits >= 40 ? n.M : std::min<int64_t>(n.M, int64_t(1) << xp_bits));
+    if (n.pbound < 1) n.pbound = 1;
     int cur = total;
     n.shift.clear();
     n.pack_col.clear();
@@ -959,6 +982,7 @@ const char* figaro_error_string(int s) {
     case FIGARO_ERR_KEY_RANGE: return "FIGARO_ERR_KEY_RANGE";
     case FIGARO_ERR_NOT_SORTED: return "FIGARO_ERR_NOT_SORTED";
     case FIGARO_ERR_UNSUPPORTED: return "FIGARO_ERR_UNSUPPORTED";
+    case FIGARO_ERR_SINGULAR: return "FIGARO_ERR_SINGULAR";
     default: return "FIGARO_ERR_UNKNOWN";
   }
 }
@@ -1090,11 +1114,16 @@ int figaro_plan(const figaro_join_tree* tree, const figaro_options* opt, void* s
     if (e != cudaSuccess) return bail(e, "cudaEventCreate");
   }
   // static tables: column descriptors, block column maps, block list, beta table
-  for (auto& n : P->nodes)
+  for (auto& n : P->nodes) {
     if (!n.coldesc.empty()) {
       e = cudaMemcpyAsync(n.b.coldesc, n.coldesc.data(), n.coldesc.size() * sizeof(int2), cudaMemcpyHostToDevice, P->st);
       if (e != cudaSuccess) return bail(e, "upload column map");
     }
+    if (n.g_colkind) {
+      e = cudaMemcpyAsync(n.g_colkind, n.colkind.data(), n.colkind.size(), cudaMemcpyHostToDevice, P->st);
+      if (e != cudaSuccess) return bail(e, "upload column kinds");
+    }
+  }
   std::vector<std::vector<int>> cols(P->blocks.size());
   for (size_t bi = 0; bi < P->blocks.size(); ++bi) {
     cols[bi] = block_cols(*P, bi);
@@ -1168,6 +1197,89 @@ int figaro_pca(figaro_plan_t p, int32_t k, double* components, double* eigvals) 
   square_values(p->sig, ev, k, p->st, &p->launches);
   if (host) FIG_CUDA(cudaMemcpyAsync(eigvals, ev, k * sizeof(double), cudaMemcpyDeviceToHost, p->st));
   return finish(*p, 8);
+}
+
+int figaro_backward(figaro_plan_t p, const double* R, int64_t ldr, const double* Rbar, int64_t ldb,
+                    double* const* grads, const int64_t* ldg) {
+  using namespace fig;
+  g_last_error.clear();
+  if (!p || !R || !Rbar || !grads || !ldg) return fail(FIGARO_ERR_INVALID_ARG, "null argument");
+  if (ldr < p->N || ldb < p->N) return fail(FIGARO_ERR_INVALID_ARG, "ldr or ldb < N");
+  if (!p->opt.gradients) return fail(FIGARO_ERR_UNSUPPORTED, "plan made without gradients = 1");
+  if (p->opt.mem != FIGARO_MEM_DEVICE) return fail(FIGARO_ERR_UNSUPPORTED, "gradients need device memory");
+  const int r = (int)p->nodes.size();
+  for (int i = 0; i < r; ++i)
+    if (p->nodes[i].N > 0 && (!grads[i] || ldg[i] < p->nodes[i].M))
+      return fail(FIGARO_ERR_INVALID_ARG, "gradient buffer of relation " + std::to_string(i));
+  figaro_plan_s& P = *p;
+  cudaStream_t st = P.st;
+  const int N = P.N;
+  const int64_t NN = (int64_t)N * N;
+  FIG_CUDA(cudaMemsetAsync(P.err_dev, 0, sizeof(int), st));
+  grad_w(R, ldr, Rbar, ldb, N, P.grad_w, P.grad_w + NN, P.grad_w + 2 * NN, P.err_dev, st);
+  auto view = [&](int i) {
+    Node& n = P.nodes[i];
+    GradNode g{};
+    g.N = N;
+    g.Ni = n.N;
+    g.col_off = n.col_off;
+    g.n_child = (int)n.children.size();
+    g.is_root = n.root;
+    g.M = n.M;
+    g.sizes = n.b.sizes;
+    g.goff = n.b.goff;
+    g.g2p = n.b.g2p;
+    g.row_gid = n.b.row_gid;
+    g.perm = n.b.sperm;
+    g.heads = n.b.heads;
+    g.ldh = n.M;
+    g.hrow = n.b.hrow;
+    g.phic = n.b.phic;
+    g.phiu = n.b.phiu;
+    g.q = n.b.q;
+    for (int c = 0; c < g.n_child; ++c) {
+      const Node& ch = P.nodes[n.children[c]];
+      g.cphid[c] = ch.b.phid;
+      g.cup[c] = ch.g_up;
+      g.cld[c] = ch.pbound;
+    }
+    g.colkind = n.g_colkind;
+    g.up = n.g_up;
+    g.ldu = n.pbound;
+    g.dn = n.g_dn;
+    g.ldd = n.pbound;
+    g.W = P.grad_w;
+    g.phi = n.g_phi;
+    g.data = n.data;
+    g.rs = n.layout == FIGARO_COL_MAJOR ? 1 : n.ld;
+    g.cs = n.layout == FIGARO_COL_MAJOR ? n.ld : 1;
+    g.grad = grads[i];
+    g.ldg = ldg[i];
+    return g;
+  };
+  for (int i = 0; i < r; ++i) {
+    Node& n = P.nodes[i];
+    grad_clear(n.g_up, n.pbound, n.b.sizes, N, n.pbound, st);
+    grad_clear(n.g_dn, n.pbound, n.b.sizes, N, n.pbound, st);
+  }
+  for (int i : P.post)
+    if (!P.nodes[i].root) grad_up(view(i), P.nodes[i].M, st);
+  for (int i : P.pre) {
+    Node& n = P.nodes[i];
+    for (int j = 0; j < (int)n.children.size(); ++j) {
+      Node& ch = P.nodes[n.children[j]];
+      grad_down(view(i), j, ch.g_dn, ch.pbound, n.M, st);
+    }
+  }
+  for (int i = 0; i < r; ++i)
+    if (P.nodes[i].N > 0) grad_rows(view(i), P.nodes[i].M, st);
+  FIG_CUDA(cudaGetLastError());
+  FIG_CUDA(cudaMemcpyAsync(P.err_host, P.err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+  FIG_CUDA(cudaStreamSynchronize(st));
+  if (P.err_host[0] != FIGARO_OK)
+    return fail(P.err_host[0], P.err_host[0] == FIGARO_ERR_SINGULAR ? "R has a zero diagonal entry"
+                                                                    : "device error in figaro_backward");
+  return FIGARO_OK;
 }
 
 int figaro_plan_get_info(figaro_plan_t p, figaro_plan_info* info) {

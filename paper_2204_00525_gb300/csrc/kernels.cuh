@@ -238,4 +238,43 @@ void gram_add(const TsqrBlock& b, const double* partial, double* G, int N, cudaS
 void refine_r(double* R, int64_t ldr, const double* G, int N, double* W1, double* W2, int* ok, cudaStream_t st,
               int64_t* launches);
 
+// ------------------------------------------------------------------ grad.cu
+// One relation's view for the gradient kernels (see grad.cu).
+struct GradNode {
+  int N, Ni, col_off, n_child, is_root;
+  int64_t M;
+  const int32_t* sizes;      // G, P
+  const int32_t* goff;
+  const int32_t* g2p;
+  const int32_t* row_gid;
+  const int32_t* perm;       // sorted position -> input row (null: identity)
+  const double* heads;       // finished heads S(g) / sqrt(rows), [col][g], ld ldh
+  int64_t ldh;
+  const double* hrow;        // 1 / sqrt(rows)
+  const uint64_t* phic;      // Phi_circ per group
+  const uint64_t* phiu;      // Phi_up per parent group (not the root)
+  const int32_t* q;          // [child][M]: index of the group's key among the child's X_p keys
+  const uint64_t* cphid[kMaxChildren];   // children's Phi_down
+  const double* cup[kMaxChildren];       // children's up messages [col][x], ld cld
+  int64_t cld[kMaxChildren];
+  const uint8_t* colkind;    // [N]: 0 own column, 1 + c child c's subtree, 255 the rest
+  double* up;                // own up message [col][x_p], ld ldu
+  int64_t ldu;
+  const double* dn;          // own down message [col][x_p], ld ldd (not the root)
+  int64_t ldd;
+  const double* W;           // N x N row-major
+  double* phi;               // [a][g], ld M
+  const double* data;        // the relation's data: element (row r, column b) at r * rs + b * cs
+  int64_t rs, cs;
+  double* grad;              // output, column-major, ld ldg (input row order)
+  int64_t ldg;
+};
+
+void grad_w(const double* R, int64_t ldr, const double* Rbar, int64_t ldb, int N, double* W, double* T1, double* T2,
+            int* err, cudaStream_t st);
+void grad_clear(double* a, int64_t ld, const int32_t* sizes, int N, int64_t bound, cudaStream_t st);
+void grad_up(const GradNode& g, int64_t bound, cudaStream_t st);
+void grad_down(const GradNode& g, int j, double* dn_child, int64_t ld_child, int64_t bound, cudaStream_t st);
+void grad_rows(const GradNode& g, int64_t bound, cudaStream_t st);
+
 }  // namespace fig
