@@ -160,6 +160,50 @@ def run_plan_only(args):
     log(f"{args.plan_only}: {ms:.3f} ms per step")
 
 
+def run_batch(args):
+    """--batch-instances K: the first K instances of the 256-instance batch workload
+    (two-relation joins, 1k-1M rows per side, 8-64 columns): R and the top-min(10, n)
+    principal components of every instance, as one graph launch (figaro_batch_run)
+    against the same plans called one after another.  Prints one JSON line."""
+    import torch
+    from paper_2204_00525_gb300 import binding
+    binding.load(build_if_missing=True)
+    t0 = time.time()
+    dbs = [synth.batch_instance(i) for i in range(args.batch_instances)]
+    cells = sum(db.input_cells() for db in dbs)
+    plans = [binding.plan_from_db(db) for db in dbs]
+    ks = [min(10, db.n_cols) for db in dbs]
+    log(f"batch: {len(dbs)} instances, {cells / 1e6:.1f}M cells, setup {time.time() - t0:.1f}s")
+    for _ in range(args.warmup):                      # one call each: graphs captured
+        for p, k in zip(plans, ks):
+            p.pca(k)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        for p, k in zip(plans, ks):
+            p.qr_r()
+            p.pca(k)
+    loop_ms = (time.perf_counter() - t) * 1e3 / args.steps
+    bt = binding.Batch(plans, k=ks)
+    for _ in range(args.warmup):
+        bt.run()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        bt.run()
+    batch_ms = (time.perf_counter() - t) * 1e3 / args.steps
+    out = {"metric": "batched instances: R and top-10 PCA of every instance", "impl": "figaro-batch",
+           "value": len(dbs) / (batch_ms * 1e-3), "unit": "instances/s", "ms_per_batch": batch_ms,
+           "cells_per_s": cells / (batch_ms * 1e-3), "loop_ms": loop_ms, "speedup_vs_loop": loop_ms / batch_ms,
+           "launches_per_batch": bt.launches(), "instances": len(dbs), "input_cells": cells,
+           "steps": args.steps, "warmup": args.warmup, "dtype": "f64", "data": "synthetic (seeded)",
+           "timing": "host clock around figaro_batch_run (launch + wait) / around the loop of "
+                     "figaro_qr_r + figaro_pca calls (each waits)"}
+    bt.close()
+    for p in plans:
+        p.close()
+    print(json.dumps(out), flush=True)
+
+
 def run_figaro(args):
     import torch
     from paper_2204_00525_gb300 import binding
@@ -387,11 +431,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plan-only", choices=["fp64", "mixed", "fp64-staged", "mixed-staged"],
                     help="profiling aid: run one plan only and print no JSON line")
+    ap.add_argument("--batch-instances", type=int, default=0,
+                    help="measure the batched-instances workload (first K of 256) instead")
     args = ap.parse_args()
     if args.warmup < 3:
         log("warning: fewer than 3 warm-up steps")
     if args.plan_only:
         run_plan_only(args)
+    elif args.batch_instances:
+        run_batch(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -192,6 +192,28 @@ int figaro_pca(figaro_plan_t plan, int32_t k, double* components, double* eigval
 int figaro_backward(figaro_plan_t plan, const double* R, int64_t ldr, const double* Rbar, int64_t ldb,
                     double* const* grads, const int64_t* ldg);
 
+/* Batches of independent instances (many joins, each with its own plan) as one CUDA
+ * graph: every plan's R pipeline, and with k[i] > 0 its Jacobi SVD and top-k principal
+ * components, become independent branches of one graph that figaro_batch_run launches
+ * at once, so that small and uneven instances overlap on the GPU.  The paper treats one
+ * join at a time; batching is not part of it.
+ *   plans       n distinct plans (device memory, stage_timing = 0).  Their inputs are
+ *               read at every run; a plan must not be used elsewhere while a run is in
+ *               flight.
+ *   R[i]        device, N_i x N_i row-major (ld N_i): instance i's R.
+ *   components, eigvals, k   NULL, or per instance: k[i] in [0, N_i]; when k[i] > 0,
+ *               components[i] (device, N_i x k[i] row-major) and eigvals[i] (device, k[i])
+ *               as figaro_pca writes them.
+ * figaro_batch_run launches the graph and waits; status (NULL or n entries) receives each
+ * instance's error word, and the first non-zero one is returned.  figaro_batch_launches
+ * is the number of kernels one run launches.                                          */
+typedef struct figaro_batch_s* figaro_batch_t;
+int figaro_batch_create(int32_t n, const figaro_plan_t* plans, double* const* R, double* const* components,
+                        double* const* eigvals, const int32_t* k, figaro_batch_t* out);
+int figaro_batch_run(figaro_batch_t batch, int32_t* status);
+int64_t figaro_batch_launches(figaro_batch_t batch);
+int figaro_batch_destroy(figaro_batch_t batch);
+
 /* Release the plan's workspace (waits for its stream).  NULL is accepted. */
 int figaro_plan_destroy(figaro_plan_t plan);
 

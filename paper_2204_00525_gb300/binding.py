@@ -84,6 +84,10 @@ def load(build_if_missing: bool = False):
         "figaro_debug_read": (C.c_int64, [P, C.c_int32, C.c_int32, P, C.c_int64]),
         "figaro_svd_from_r_static": (C.c_int, [P, C.c_int64, C.c_int32, P, P, P]),
         "figaro_backward": (C.c_int, [P, P, C.c_int64, P, C.c_int64, P, P]),
+        "figaro_batch_create": (C.c_int, [C.c_int32, P, P, P, P, P, C.POINTER(P)]),
+        "figaro_batch_run": (C.c_int, [P, P]),
+        "figaro_batch_launches": (C.c_int64, [P]),
+        "figaro_batch_destroy": (C.c_int, [P]),
         "figaro_error_string": (C.c_char_p, [C.c_int]),
         "figaro_last_error": (C.c_char_p, []),
     }
@@ -363,4 +367,52 @@ class FigaroR:
 
     def __call__(self, *datas):
         return self._fn.apply(*datas)
+
+
+class Batch:
+    """Many JoinPlans run as one CUDA graph (figaro_batch_*): R of every instance, and the
+    top-k principal components where k[i] > 0."""
+
+    def __init__(self, plans, k=None):
+        import torch
+        lib = load()
+        n = len(plans)
+        self.plans = plans
+        self.R = [torch.empty(p.n_cols, p.n_cols, dtype=torch.float64, device="cuda") for p in plans]
+        self.k = [0] * n if k is None else [int(x) for x in k]
+        self.comps = [torch.empty(p.n_cols, max(ki, 1), dtype=torch.float64, device="cuda")
+                      for p, ki in zip(plans, self.k)]
+        self.eig = [torch.empty(max(ki, 1), dtype=torch.float64, device="cuda") for ki in self.k]
+        arr = lambda xs: (C.c_void_p * n)(*[x for x in xs])
+        self._arrays = [arr([p.handle for p in plans]), arr([t.data_ptr() for t in self.R]),
+                        arr([t.data_ptr() for t in self.comps]), arr([t.data_ptr() for t in self.eig]),
+                        (C.c_int32 * n)(*self.k)]
+        h = C.c_void_p()
+        check(lib.figaro_batch_create(n, C.cast(self._arrays[0], C.c_void_p), C.cast(self._arrays[1], C.c_void_p),
+                                      C.cast(self._arrays[2], C.c_void_p), C.cast(self._arrays[3], C.c_void_p),
+                                      C.cast(self._arrays[4], C.c_void_p), C.byref(h)))
+        self.handle = h
+
+    def run(self):
+        """Launch every instance and wait; returns the per-instance status list."""
+        n = len(self.plans)
+        st = (C.c_int32 * n)()
+        rc = load().figaro_batch_run(self.handle, C.cast(st, C.c_void_p))
+        self.status = list(st)
+        check(rc)
+        return self.status
+
+    def launches(self):
+        return int(load().figaro_batch_launches(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            load().figaro_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 

@@ -130,6 +130,15 @@ struct figaro_plan_s {
   double* grad_w = nullptr;            // gradients: W and two N x N work arrays
 };
 
+struct figaro_batch_s {
+  std::vector<figaro_plan_t> plans;
+  cudaStream_t st = nullptr;           // the batch graph runs here
+  cudaGraphExec_t exec = nullptr;
+  int* status_dev = nullptr;           // [n] every instance's error word, gathered
+  int* status_host = nullptr;          // pinned copy
+  int64_t launches = 0;
+};
+
 namespace fig {
 
 // ------------------------------------------------------------------ arena
@@ -1198,6 +1207,128 @@ int figaro_pca(figaro_plan_t p, int32_t k, double* components, double* eigvals) 
   if (host) FIG_CUDA(cudaMemcpyAsync(eigvals, ev, k * sizeof(double), cudaMemcpyDeviceToHost, p->st));
   return finish(*p, 8);
 }
+
+// ------------------------------------------------------------------ batches of instances
+namespace fig {
+__global__ void k_gather_status(int* const* words, int n, int* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = *words[i];
+}
+}  // namespace fig
+
+int figaro_batch_destroy(figaro_batch_t b) {
+  if (!b) return FIGARO_OK;
+  if (b->st) cudaStreamSynchronize(b->st);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->status_dev) cudaFree(b->status_dev);
+  if (b->status_host) cudaFreeHost(b->status_host);
+  if (b->st) cudaStreamDestroy(b->st);
+  delete b;
+  return FIGARO_OK;
+}
+
+int figaro_batch_create(int32_t n, const figaro_plan_t* plans, double* const* R, double* const* components,
+                        double* const* eigvals, const int32_t* k, figaro_batch_t* out) {
+  using namespace fig;
+  g_last_error.clear();
+  if (!out || n < 1 || !plans || !R) return fail(FIGARO_ERR_INVALID_ARG, "null argument or n < 1");
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    const figaro_plan_t p = plans[i];
+    if (!p || !R[i]) return fail(FIGARO_ERR_INVALID_ARG, "null plan or R of instance " + std::to_string(i));
+    if (p->opt.mem != FIGARO_MEM_DEVICE || p->opt.stage_timing)
+      return fail(FIGARO_ERR_UNSUPPORTED, "batched plans need device memory and no stage timing");
+    const int ki = k ? k[i] : 0;
+    if (ki < 0 || ki > p->N || (ki > 0 && (!components || !eigvals || !components[i] || !eigvals[i])))
+      return fail(FIGARO_ERR_INVALID_ARG, "PCA outputs of instance " + std::to_string(i));
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == p) return fail(FIGARO_ERR_INVALID_ARG, "a plan appears twice in the batch");
+  }
+  auto* B = new (std::nothrow) figaro_batch_s();
+  if (!B) return fail(FIGARO_ERR_NOMEM, "host allocation");
+  B->plans.assign(plans, plans + n);
+  auto bail = [&](cudaError_t e, const char* what) {
+    figaro_batch_destroy(B);
+    return fail(FIGARO_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  };
+  cudaError_t e = cudaStreamCreateWithFlags(&B->st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc(&B->status_dev, sizeof(int) * (n + 1) + sizeof(int*) * n);
+  if (e == cudaSuccess) e = cudaMallocHost(&B->status_host, sizeof(int) * n);
+  if (e != cudaSuccess) return bail(e, "batch setup");
+  int** words = reinterpret_cast<int**>(B->status_dev + n + (n & 1));
+  {
+    std::vector<int*> w(n);
+    for (int i = 0; i < n; ++i) w[i] = plans[i]->err_dev;
+    e = cudaMemcpy(words, w.data(), sizeof(int*) * n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bail(e, "batch setup");
+  }
+  // one capture: every plan's pipeline on its own streams, forked from and joined to the
+  // batch stream, so the instances are independent branches of one graph
+  cudaEvent_t fork = nullptr;
+  e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  if (e != cudaSuccess) return bail(e, "batch event");
+  std::vector<cudaStream_t> saved(n);
+  cudaGraph_t g = nullptr;
+  int rc = FIGARO_OK;
+  e = cudaStreamBeginCapture(B->st, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) e = cudaEventRecord(fork, B->st);
+  for (int i = 0; i < n && e == cudaSuccess && rc == FIGARO_OK; ++i) {
+    figaro_plan_s& P = *plans[i];
+    saved[i] = P.st;
+    P.st = P.exec;
+    e = cudaStreamWaitEvent(P.exec, fork, 0);
+    if (e != cudaSuccess) break;
+    rc = enqueue_r(P, P.Rtmp, P.N);
+    const int ki = k ? k[i] : 0;
+    if (rc == FIGARO_OK && ki > 0) {
+      jacobi_svd(P.Rtmp, P.N, P.N, P.svdW, P.svdV, P.sig, P.Vtmp, P.err_dev, P.exec, &B->launches);
+      e = cudaMemcpy2DAsync(components[i], ki * sizeof(double), P.Vtmp, P.N * sizeof(double), ki * sizeof(double),
+                            P.N, cudaMemcpyDeviceToDevice, P.exec);
+      if (e == cudaSuccess) square_values(P.sig, eigvals[i], ki, P.exec, &B->launches);
+    }
+    if (rc == FIGARO_OK && e == cudaSuccess)
+      e = cudaMemcpyAsync(R[i], P.Rtmp, (size_t)P.N * P.N * sizeof(double), cudaMemcpyDeviceToDevice, P.exec);
+    B->launches += P.launches;
+    if (rc == FIGARO_OK && e == cudaSuccess) e = cudaEventRecord(P.join_out, P.exec);
+    if (rc == FIGARO_OK && e == cudaSuccess) e = cudaStreamWaitEvent(B->st, P.join_out, 0);
+  }
+  if (e == cudaSuccess && rc == FIGARO_OK) {
+    k_gather_status<<<1, 256, 0, B->st>>>(words, n, B->status_dev);
+    ++B->launches;
+    e = cudaMemcpyAsync(B->status_host, B->status_dev, sizeof(int) * n, cudaMemcpyDeviceToHost, B->st);
+  }
+  cudaError_t e_end = cudaStreamEndCapture(B->st, &g);
+  for (int i = 0; i < n; ++i)
+    if (saved[i]) plans[i]->st = saved[i];
+  cudaEventDestroy(fork);
+  if (e == cudaSuccess) e = e_end;
+  if (e == cudaSuccess && rc == FIGARO_OK) e = cudaGraphInstantiate(&B->exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (rc != FIGARO_OK) {
+    cudaGetLastError();
+    figaro_batch_destroy(B);
+    return rc;
+  }
+  if (e != cudaSuccess) return bail(e, "batch graph");
+  *out = B;
+  return FIGARO_OK;
+}
+
+int figaro_batch_run(figaro_batch_t b, int32_t* status) {
+  g_last_error.clear();
+  if (!b) return fail(FIGARO_ERR_INVALID_ARG, "null batch");
+  FIG_CUDA(cudaGraphLaunch(b->exec, b->st));
+  FIG_CUDA(cudaStreamSynchronize(b->st));
+  FIG_CUDA(cudaGetLastError());
+  int first = FIGARO_OK;
+  for (size_t i = 0; i < b->plans.size(); ++i) {
+    if (status) status[i] = b->status_host[i];
+    if (first == FIGARO_OK && b->status_host[i] != FIGARO_OK) first = b->status_host[i];
+  }
+  if (first != FIGARO_OK) return fail(first, "an instance of the batch failed (see the status array)");
+  return FIGARO_OK;
+}
+
+int64_t figaro_batch_launches(figaro_batch_t b) { return b ? b->launches : -1; }
 
 int figaro_backward(figaro_plan_t p, const double* R, int64_t ldr, const double* Rbar, int64_t ldb,
                     double* const* grads, const int64_t* ldg) {
