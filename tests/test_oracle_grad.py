@@ -110,3 +110,29 @@ def test_join_sums_count_is_phi_circ():
         for gi in range(len(starts) - 1):
             rows = order[starts[gi]:starts[gi + 1]]
             assert np.all(c[rows] == bf[k]["circ"].get(tuple(int(v) for v in uniq[gi]), 0))
+
+
+def test_centered_pca_from_r_matches_materialized():
+    """Centred PCA through R and the join's column sums (from the join sums of oracle/grad:
+    sum_t c(t) y_t per relation) against the eigen-decomposition of the centred,
+    materialised join."""
+    from oracle import spectral as osp
+    for db in tiny_dbs():
+        db = orl.full_reduce(db)
+        A = orl.join_matrix(db)
+        R = ofg.figaro_r(db)
+        off = orl.col_offsets(db)
+        colsum = np.zeros(db.n_cols)
+        for k, rel in enumerate(db.relations):
+            c, _ = ogd.join_sums(db, k)
+            colsum[off[k]:off[k] + rel.n_data] = (c[:, None] * rel.data).sum(axis=0)
+        assert np.allclose(colsum, A.sum(axis=0), rtol=1e-12, atol=1e-9)
+        k = min(3, db.n_cols)
+        V1, l1 = osp.centered_pca_materialized(A, k)
+        V2, l2 = osp.centered_pca_of_r(R, colsum, A.shape[0], k)
+        assert np.allclose(l1, l2, rtol=1e-9, atol=1e-9 * abs(l1[0]))
+        lam = np.linalg.eigvalsh((A - A.mean(0)).T @ (A - A.mean(0)))[::-1]
+        gaps = np.abs(np.diff(lam[:k + 1])) > 1e-6 * lam[0]
+        for j in range(k):
+            if gaps[j] and (j == 0 or gaps[j - 1]):
+                assert min(np.linalg.norm(V1[:, j] - V2[:, j]), np.linalg.norm(V1[:, j] + V2[:, j])) < 1e-7
