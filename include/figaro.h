@@ -173,6 +173,16 @@ int figaro_svd(figaro_plan_t plan, double* sigma, double* V, double* R);
  * 1 <= k <= N. */
 int figaro_pca(figaro_plan_t plan, int32_t k, double* components, double* eigvals);
 
+/* Centred PCA (not in the paper, whose experiments do not centre): the top-k eigenvectors
+ * and eigenvalues of the scatter matrix of the centred join rows,
+ * (A - 1 mu^T)^T (A - 1 mu^T) = R^T R - |J| mu mu^T, mu the column means over the join and
+ * |J| its row count.  The column sums come from the heads and Phi_circ (sum over the
+ * groups of Phi_circ(g) S(g)), |J| from the root's full_join_size (Alg. 3), then the
+ * one-sided Jacobi SVD of the N x N scatter matrix (symmetric positive semi-definite: its
+ * singular values are its eigenvalues).  components: N x k row-major; eigvals: k values,
+ * descending (not divided by |J|).  Same memory rules as figaro_pca.                  */
+int figaro_pca_centered(figaro_plan_t plan, int32_t k, double* components, double* eigvals);
+
 /* Gradient of a loss L(R) with respect to every relation's data columns, at the data of
  * the last figaro_qr_r / figaro_svd / figaro_pca call on this plan (made with
  * gradients = 1 and mem = FIGARO_MEM_DEVICE).  The paper does not differentiate R; with

@@ -84,6 +84,7 @@ def load(build_if_missing: bool = False):
         "figaro_debug_read": (C.c_int64, [P, C.c_int32, C.c_int32, P, C.c_int64]),
         "figaro_svd_from_r_static": (C.c_int, [P, C.c_int64, C.c_int32, P, P, P]),
         "figaro_backward": (C.c_int, [P, P, C.c_int64, P, C.c_int64, P, P]),
+        "figaro_pca_centered": (C.c_int, [P, C.c_int32, P, P]),
         "figaro_batch_create": (C.c_int, [C.c_int32, P, P, P, P, P, C.POINTER(P)]),
         "figaro_batch_run": (C.c_int, [P, P]),
         "figaro_batch_launches": (C.c_int64, [P]),
@@ -265,6 +266,11 @@ class JoinPlan:
     def pca(self, k):
         comp, ev = self._out(self.n_cols, k), self._out(k)
         figaro_pca(self.handle, k, comp.data_ptr(), ev.data_ptr())
+        return comp, ev
+
+    def pca_centered(self, k):
+        comp, ev = self._out(self.n_cols, k), self._out(k)
+        check(load().figaro_pca_centered(self.handle, k, C.c_void_p(comp.data_ptr()), C.c_void_p(ev.data_ptr())))
         return comp, ev
 
     def backward(self, R, Rbar):

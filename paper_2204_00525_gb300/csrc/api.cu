@@ -128,6 +128,9 @@ struct figaro_plan_s {
   int* refine_ok = nullptr;            // device: 1 when the last refinement was applied
   int refined = 0;
   double* grad_w = nullptr;            // gradients: W and two N x N work arrays
+  double* colsum = nullptr;            // centred PCA: column sums of A, |J|, scatter matrix
+  unsigned long long* jsize = nullptr;
+  double* scatter = nullptr;
 };
 
 struct figaro_batch_s {
@@ -253,6 +256,9 @@ static void layout(figaro_plan_s& P, Arena& a) {
   const int64_t NN = (int64_t)P.N * P.N;
   P.Rtmp = a.take<double>(NN);
   if (P.opt.gradients) P.grad_w = a.take<double>(3 * NN);
+  P.colsum = a.take<double>(P.N);
+  P.jsize = a.take<unsigned long long>(1);
+  P.scatter = a.take<double>(NN);
   P.gram_partial.assign(P.blocks.size(), nullptr);
   if (refine) {
     for (size_t bi = 0; bi < P.blocks.size(); ++bi) P.gram_partial[bi] = a.take<double>(gram_partial_elems(P.blocks[bi]));
@@ -1329,6 +1335,28 @@ int figaro_batch_run(figaro_batch_t b, int32_t* status) {
 }
 
 int64_t figaro_batch_launches(figaro_batch_t b) { return b ? b->launches : -1; }
+
+int figaro_pca_centered(figaro_plan_t p, int32_t k, double* components, double* eigvals) {
+  using namespace fig;
+  g_last_error.clear();
+  if (!p || !components || !eigvals) return fail(FIGARO_ERR_INVALID_ARG, "null argument");
+  if (k < 1 || k > p->N) return fail(FIGARO_ERR_INVALID_ARG, "k must be in [1, N]");
+  figaro_plan_s& P = *p;
+  int rc = run_r(P, P.Rtmp, P.N);
+  if (rc != FIGARO_OK) return rc;
+  cudaStream_t st = P.st;
+  for (auto& n : P.nodes)
+    join_colsum(n.b.heads, n.M, n.b.goff, n.b.hrow, n.b.phic, n.b.sizes, n.N, P.colsum + n.col_off, st, &P.launches);
+  join_size(P.nodes[P.root].b.full, P.nodes[P.root].b.sizes, P.jsize, st, &P.launches);
+  center_gram(P.Rtmp, P.N, P.colsum, P.jsize, P.scatter, st, &P.launches);
+  jacobi_svd(P.scatter, P.N, P.N, P.svdW, P.svdV, P.sig, P.Vtmp, P.err_dev, st, &P.launches);
+  const bool host = P.opt.mem == FIGARO_MEM_HOST;
+  const cudaMemcpyKind kind = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  FIG_CUDA(cudaMemcpy2DAsync(components, k * sizeof(double), P.Vtmp, P.N * sizeof(double), k * sizeof(double), P.N,
+                             kind, st));
+  FIG_CUDA(cudaMemcpyAsync(eigvals, P.sig, k * sizeof(double), kind, st));
+  return finish(P, 8);
+}
 
 int figaro_backward(figaro_plan_t p, const double* R, int64_t ldr, const double* Rbar, int64_t ldb,
                     double* const* grads, const int64_t* ldg) {

@@ -229,6 +229,12 @@ cudaError_t svd_set_attributes();
 void jacobi_svd(const double* R, int64_t ldr, int N, double* W, double* V, double* sigma,
                 double* Vout, int* err, cudaStream_t st, int64_t* launches);
 void square_values(const double* s, double* out, int k, cudaStream_t st, int64_t* launches);
+void join_colsum(const double* heads, int64_t ldh, const int32_t* goff, const double* hrow, const uint64_t* phic,
+                 const int32_t* sizes, int n, double* out, cudaStream_t st, int64_t* launches);
+void join_size(const uint64_t* full, const int32_t* sizes, unsigned long long* out, cudaStream_t st,
+               int64_t* launches);
+void center_gram(const double* R, int N, const double* colsum, const unsigned long long* join_size, double* C,
+                 cudaStream_t st, int64_t* launches);
 
 // ------------------------------------------------------------------ refine.cu
 cudaError_t refine_set_attributes();

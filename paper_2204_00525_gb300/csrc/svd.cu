@@ -129,6 +129,76 @@ void jacobi_svd(const double* R, int64_t ldr, int N, double* W, double* V, doubl
   ++*launches;
 }
 
+// ------------------------------------------------------------------ centred PCA
+// Column sums of the join matrix, relation by relation: sum over the tuples t of c(t) y_t
+// (c(t) = Phi_circ of t's group, Fig. 4) = sum over the groups g of Phi_circ(g) S(g), with
+// the group sums S(g) = head(g) sqrt(rows).  One block per column, threads over groups
+// in a fixed order (deterministic).
+__global__ void __launch_bounds__(1024) k_join_colsum(const double* heads, int64_t ldh, const int32_t* goff,
+                                                      const double* hrow, const uint64_t* phic, const int32_t* sizes,
+                                                      double* out) {
+  __shared__ double red[33];
+  const int a = blockIdx.x;
+  const int64_t G = sizes[0];
+  double s = 0.0;
+  for (int64_t g = threadIdx.x; g < G; g += blockDim.x) {
+    const double rows = (double)(goff[g + 1] - goff[g]);
+    s = fma((double)phic[g], heads[(int64_t)a * ldh + g] * rows * hrow[g], s);
+  }
+  s = block_sum<double>(s, red);
+  if (threadIdx.x == 0) out[a] = s;
+}
+
+// |J| = sum over the root's groups of full_join_size (exact in uint64).
+__global__ void k_join_size(const uint64_t* full, const int32_t* sizes, unsigned long long* out) {
+  __shared__ unsigned long long red[32];
+  const int64_t G = sizes[0];
+  unsigned long long s = 0;
+  for (int64_t g = threadIdx.x; g < G; g += blockDim.x) s += full[g];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    *out = t;
+  }
+}
+
+// C = R^T R - colsum colsum^T / |J| (N x N, row-major), the scatter matrix of the centred
+// join rows.
+__global__ void k_center_gram(const double* R, int N, const double* colsum, const unsigned long long* join_size,
+                              double* C) {
+  const double inv = *join_size ? 1.0 / (double)*join_size : 0.0;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)N * N;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / N), j = (int)(idx % N);
+    const int kmax = i < j ? i : j;
+    double s = 0.0;
+    for (int k = 0; k <= kmax; ++k) s = fma(R[(int64_t)k * N + i], R[(int64_t)k * N + j], s);
+    C[idx] = s - colsum[i] * colsum[j] * inv;
+  }
+}
+
+void join_colsum(const double* heads, int64_t ldh, const int32_t* goff, const double* hrow, const uint64_t* phic,
+                 const int32_t* sizes, int n, double* out, cudaStream_t st, int64_t* launches) {
+  if (n <= 0) return;
+  k_join_colsum<<<n, 1024, 0, st>>>(heads, ldh, goff, hrow, phic, sizes, out);
+  ++*launches;
+}
+
+void join_size(const uint64_t* full, const int32_t* sizes, unsigned long long* out, cudaStream_t st,
+               int64_t* launches) {
+  k_join_size<<<1, 1024, 0, st>>>(full, sizes, out);
+  ++*launches;
+}
+
+void center_gram(const double* R, int N, const double* colsum, const unsigned long long* join_size, double* C,
+                 cudaStream_t st, int64_t* launches) {
+  k_center_gram<<<grid_for((int64_t)N * N, 256, 152), 256, 0, st>>>(R, N, colsum, join_size, C);
+  ++*launches;
+}
+
 void square_values(const double* s, double* out, int k, cudaStream_t st, int64_t* launches) {
   k_square<<<1, 256, 0, st>>>(s, out, k);
   ++*launches;

@@ -401,3 +401,42 @@ def test_full_size_path_join_refined(path3_full):
     assert rel_err(R, np.linalg.cholesky(G).T) < 1e-9
     lam = np.linalg.eigvalsh(G)[::-1]
     assert np.max(np.abs(s.cpu().numpy() ** 2 - lam)) / lam[0] < 1e-10
+
+
+# ------------------------------------------------------------------ centred PCA
+
+@pytest.mark.parametrize("name", ["two_relation", "four_relation", "path3", "star"])
+def test_centered_pca(name):
+    """figaro_pca_centered against the eigen-decomposition of the centred scatter matrix:
+    materialised join for the small shapes, R and the oracle's join column sums beyond."""
+    from oracle import grad as ogd
+    dbs = {"two_relation": synth.two_relation(seed=1, rows=200, keys=20),
+           "four_relation": synth.four_relation(seed=16, domain=3, rows=(12, 50, 10, 9), n_cols=(3, 2, 2, 2)),
+           "path3": synth.path3(rows=20_000, keys=300),
+           "star": synth.star(fact_rows=20_000, dim_rows=2000, keys=500, n_cols=4)}
+    db = orl.full_reduce(dbs[name])
+    k = min(5, db.n_cols)
+    p = plan_for(db)
+    comp, ev = p.pca_centered(k)
+    comp, ev = comp.cpu().numpy(), ev.cpu().numpy()
+    p.close()
+    if name in ("two_relation", "four_relation"):
+        A = orl.join_matrix(db)
+        Ac = A - A.mean(axis=0)
+        C = Ac.T @ Ac
+    else:
+        R = ofg.figaro_r(db)
+        off = orl.col_offsets(db)
+        colsum = np.zeros(db.n_cols)
+        for kk, rel in enumerate(db.relations):
+            c, _ = ogd.join_sums(db, kk)
+            colsum[off[kk]:off[kk] + rel.n_data] = (c[:, None] * rel.data).sum(axis=0)
+        n_join = ogd.join_sums(db, 0)[0].sum()      # |J| = sum over one relation's tuples of c(t)
+        C = R.T @ R - np.outer(colsum, colsum) / n_join
+    lam, W = np.linalg.eigh(C)
+    lam, W = lam[::-1], W[:, ::-1]
+    assert np.max(np.abs(ev - lam[:k])) / lam[0] < 1e-10
+    for j in range(1, k + 1):
+        gap = (lam[j - 1] - lam[j]) / lam[0] if j < len(lam) else 1.0
+        if gap > 1e-6:
+            assert np.linalg.norm(comp[:, :j] @ comp[:, :j].T - W[:, :j] @ W[:, :j].T) < 1e-10 / gap + 1e-9
