@@ -173,6 +173,27 @@ int figaro_svd(figaro_plan_t plan, double* sigma, double* V, double* R);
  * 1 <= k <= N. */
 int figaro_pca(figaro_plan_t plan, int32_t k, double* components, double* eigvals);
 
+/* Projections of the join matrix, A X (§8.1-8.3 express Q = A R^-1, U = A V Sigma^-1 and
+ * the principal-component scores A V_k through R and its SVD), at the data of the last
+ * figaro_qr_r / figaro_svd / figaro_pca call; their row count is the join size, so they
+ * are for joins that fit in memory.  The join rows come in a fixed order: the root's
+ * tuples in sorted-key order; below a tuple, the combinations of its children's subtrees
+ * in mixed radix (first child most significant); inside a child's key group, its tuples
+ * in sorted order.
+ *   mode   FIGARO_PROJ_X (A X for the caller's X: device, N x k row-major, ld ldx),
+ *          FIGARO_PROJ_Q (Q = A R^-1, k = N), FIGARO_PROJ_U (the first k columns of
+ *          U = A V Sigma^-1), FIGARO_PROJ_SCORES (A V_k, the top-k PCA scores).
+ *   R      device, N x N row-major (ld ldr): the R of that call.
+ *   out    device, rows x k row-major (ld ldo >= k).  *rows (if not NULL) receives the
+ *          join size; a join larger than max_rows is FIGARO_ERR_UNSUPPORTED (nothing is
+ *          written).  A zero diagonal of R (Q) or a zero singular value (U) is
+ *          FIGARO_ERR_SINGULAR.  Device memory only; synchronous.
+ * figaro_join_size: |J| at the data of the last call (exact).                           */
+enum { FIGARO_PROJ_X = 0, FIGARO_PROJ_Q = 1, FIGARO_PROJ_U = 2, FIGARO_PROJ_SCORES = 3 };
+int figaro_join_size(figaro_plan_t plan, uint64_t* rows);
+int figaro_project(figaro_plan_t plan, int32_t mode, const double* R, int64_t ldr, const double* X, int64_t ldx,
+                   int32_t k, double* out, int64_t ldo, int64_t max_rows, int64_t* rows);
+
 /* Centred PCA (not in the paper, whose experiments do not centre): the top-k eigenvectors
  * and eigenvalues of the scatter matrix of the centred join rows,
  * (A - 1 mu^T)^T (A - 1 mu^T) = R^T R - |J| mu mu^T, mu the column means over the join and

@@ -15,9 +15,11 @@ import os
 from . import build_lib
 
 FIGARO_OK = 0
+FIGARO_ERR_UNSUPPORTED = 10
 FIGARO_KEY_I64, FIGARO_KEY_I32 = 0, 1
 FIGARO_COL_MAJOR, FIGARO_ROW_MAJOR = 0, 1
 FIGARO_PREC_FP64, FIGARO_PREC_MIXED, FIGARO_PREC_MIXED_REFINED = 0, 1, 2
+FIGARO_PROJ_X, FIGARO_PROJ_Q, FIGARO_PROJ_U, FIGARO_PROJ_SCORES = 0, 1, 2, 3
 FIGARO_MEM_DEVICE, FIGARO_MEM_HOST = 0, 1
 DBG = {"sizes": 0, "perm": 1, "group_off": 2, "counts": 3, "pcounts": 4, "tails": 5, "heads": 6,
        "gen_tails": 7, "data": 8, "root_rows": 9}
@@ -85,6 +87,9 @@ def load(build_if_missing: bool = False):
         "figaro_svd_from_r_static": (C.c_int, [P, C.c_int64, C.c_int32, P, P, P]),
         "figaro_backward": (C.c_int, [P, P, C.c_int64, P, C.c_int64, P, P]),
         "figaro_pca_centered": (C.c_int, [P, C.c_int32, P, P]),
+        "figaro_join_size": (C.c_int, [P, C.POINTER(C.c_uint64)]),
+        "figaro_project": (C.c_int, [P, C.c_int32, P, C.c_int64, P, C.c_int64, C.c_int32, P, C.c_int64, C.c_int64,
+                                     C.POINTER(C.c_int64)]),
         "figaro_batch_create": (C.c_int, [C.c_int32, P, P, P, P, P, C.POINTER(P)]),
         "figaro_batch_run": (C.c_int, [P, P]),
         "figaro_batch_launches": (C.c_int64, [P]),
@@ -267,6 +272,31 @@ class JoinPlan:
         comp, ev = self._out(self.n_cols, k), self._out(k)
         figaro_pca(self.handle, k, comp.data_ptr(), ev.data_ptr())
         return comp, ev
+
+    def join_size(self):
+        n = C.c_uint64()
+        check(load().figaro_join_size(self.handle, C.byref(n)))
+        return int(n.value)
+
+    def project(self, R, mode=FIGARO_PROJ_Q, X=None, k=None, max_rows=1 << 27):
+        """A X for the last call's data (see figaro_project): Q (mode FIGARO_PROJ_Q), the
+        first k columns of U, the top-k PCA scores, or A X for a given X (N x k)."""
+        import torch
+        N = self.n_cols
+        if mode == FIGARO_PROJ_Q:
+            k = N
+        elif mode == FIGARO_PROJ_X:
+            X = X.to(device=R.device, dtype=torch.float64).contiguous()
+            k = X.shape[1]
+        rows = self.join_size()
+        if rows > max_rows:
+            raise FigaroError(FIGARO_ERR_UNSUPPORTED, f"the join has {rows} rows (max_rows {max_rows})")
+        out = torch.empty(max(rows, 1), k, dtype=torch.float64, device=R.device)
+        n = C.c_int64()
+        check(load().figaro_project(self.handle, mode, C.c_void_p(R.data_ptr()), R.stride(0),
+                                    C.c_void_p(X.data_ptr()) if X is not None else None, k if X is None else X.stride(0),
+                                    k, C.c_void_p(out.data_ptr()), k, max_rows, C.byref(n)))
+        return out[:rows]
 
     def pca_centered(self, k):
         comp, ev = self._out(self.n_cols, k), self._out(k)

@@ -1336,6 +1336,123 @@ int figaro_batch_run(figaro_batch_t b, int32_t* status) {
 
 int64_t figaro_batch_launches(figaro_batch_t b) { return b ? b->launches : -1; }
 
+// ------------------------------------------------------------------ projections A X
+// Theta_down prefixes of every relation (the forward forms them only for inner nodes) and
+// |J| = the root's last prefix, copied to the host.
+static int join_rows(figaro_plan_s& P, uint64_t* total) {
+  using namespace fig;
+  cudaStream_t st = P.st;
+  for (auto& n : P.nodes) {
+    ScanSrc src{SCAN_PLAIN_U64, n.b.theta, 0};
+    scan_inclusive<uint64_t>(src, n.b.theta_incl, n.M, n.b.sizes, n.b.scan_tmp_u, st, &P.launches);
+  }
+  int32_t G = 0;
+  const Node& root = P.nodes[P.root];
+  FIG_CUDA(cudaMemcpyAsync(&G, root.b.sizes, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  FIG_CUDA(cudaStreamSynchronize(st));
+  *total = 0;
+  if (G > 0) {
+    FIG_CUDA(cudaMemcpyAsync(total, root.b.theta_incl + (G - 1), sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    FIG_CUDA(cudaStreamSynchronize(st));
+  }
+  return FIGARO_OK;
+}
+
+int figaro_join_size(figaro_plan_t p, uint64_t* rows) {
+  g_last_error.clear();
+  if (!p || !rows) return fail(FIGARO_ERR_INVALID_ARG, "null argument");
+  return join_rows(*p, rows);
+}
+
+int figaro_project(figaro_plan_t p, int32_t mode, const double* R, int64_t ldr, const double* X, int64_t ldx,
+                   int32_t k, double* out, int64_t ldo, int64_t max_rows, int64_t* rows) {
+  using namespace fig;
+  g_last_error.clear();
+  if (!p || !R) return fail(FIGARO_ERR_INVALID_ARG, "null plan or R");
+  figaro_plan_s& P = *p;
+  const int N = P.N;
+  if (mode < FIGARO_PROJ_X || mode > FIGARO_PROJ_SCORES) return fail(FIGARO_ERR_INVALID_ARG, "mode");
+  if (mode == FIGARO_PROJ_Q) k = N;
+  if (k < 1 || (mode != FIGARO_PROJ_X && k > N)) return fail(FIGARO_ERR_INVALID_ARG, "k");
+  if (mode == FIGARO_PROJ_X && (!X || ldx < k)) return fail(FIGARO_ERR_INVALID_ARG, "X or ldx");
+  if (ldr < N || ldo < k) return fail(FIGARO_ERR_INVALID_ARG, "ldr or ldo");
+  if (P.opt.mem != FIGARO_MEM_DEVICE) return fail(FIGARO_ERR_UNSUPPORTED, "projections need device memory");
+  if ((int)P.nodes.size() > kMaxRel) return fail(FIGARO_ERR_UNSUPPORTED, "more than 32 relations");
+  uint64_t total = 0;
+  int rc = join_rows(P, &total);
+  if (rc != FIGARO_OK) return rc;
+  if (rows) *rows = (int64_t)total;
+  if (total > (uint64_t)(max_rows < 0 ? 0 : max_rows))
+    return fail(FIGARO_ERR_UNSUPPORTED, "the join has " + std::to_string(total) + " rows, more than max_rows");
+  if (!out) return fail(FIGARO_ERR_INVALID_ARG, "null out");
+  cudaStream_t st = P.st;
+  FIG_CUDA(cudaMemsetAsync(P.err_dev, 0, sizeof(int), st));
+  // X for the mode, N x k row-major, in the plan's scratch
+  const double* Xd = X;
+  int64_t ldxd = ldx;
+  if (mode != FIGARO_PROJ_X) {
+    if (mode == FIGARO_PROJ_Q) {
+      tri_inverse(R, ldr, N, P.scatter, P.err_dev, st);
+    } else {
+      jacobi_svd(R, ldr, N, P.svdW, P.svdV, P.sig, P.Vtmp, P.err_dev, st, &P.launches);
+      scale_v(P.Vtmp, P.sig, N, k, mode == FIGARO_PROJ_U, P.scatter, P.err_dev, st);
+    }
+    Xd = P.scatter;
+    ldxd = mode == FIGARO_PROJ_Q ? N : k;
+  }
+  // every relation's rows times its block of X
+  std::vector<double*> Pk(P.nodes.size(), nullptr);
+  auto release = [&]() {
+    for (double* q : Pk)
+      if (q) cudaFree(q);
+  };
+  for (size_t i = 0; i < P.nodes.size(); ++i) {
+    Node& n = P.nodes[i];
+    if (n.N == 0 || n.M == 0) continue;
+    if (cudaMalloc(&Pk[i], sizeof(double) * n.M * k) != cudaSuccess) {
+      cudaGetLastError();
+      release();
+      return fail(FIGARO_ERR_NOMEM, "projection buffers");
+    }
+    proj_rows(n.data, n.layout == FIGARO_COL_MAJOR ? 1 : n.ld, n.layout == FIGARO_COL_MAJOR ? n.ld : 1, n.M, n.N,
+              Xd, ldxd, n.col_off, k, Pk[i], st);
+  }
+  // the nodes in pre-order
+  std::vector<int> pos(P.nodes.size(), -1);
+  for (size_t v = 0; v < P.pre.size(); ++v) pos[P.pre[v]] = (int)v;
+  std::vector<ProjNode> pn(P.pre.size());
+  for (size_t v = 0; v < P.pre.size(); ++v) {
+    Node& n = P.nodes[P.pre[v]];
+    ProjNode& q = pn[v];
+    q.n_child = (int)n.children.size();
+    for (int c = 0; c < q.n_child; ++c) q.child[c] = pos[n.children[c]];
+    q.M = n.M;
+    q.sizes = n.b.sizes;
+    q.goff = n.b.goff;
+    q.pgoff = n.b.pgoff;
+    q.theta = n.b.theta;
+    q.theta_incl = n.b.theta_incl;
+    q.phid = n.b.phid;
+    q.q = n.b.q;
+    q.perm = n.b.sperm;
+    q.P = Pk[P.pre[v]];
+  }
+  ProjNode* pn_dev = nullptr;
+  cudaError_t e = cudaMalloc(&pn_dev, sizeof(ProjNode) * pn.size());
+  if (e == cudaSuccess) e = cudaMemcpyAsync(pn_dev, pn.data(), sizeof(ProjNode) * pn.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && total > 0) {
+    project(pn_dev, (int)pn.size(), k, total, out, ldo, st);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(P.err_host, P.err_dev, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (pn_dev) cudaFree(pn_dev);
+  release();
+  if (e != cudaSuccess) return fail(FIGARO_ERR_CUDA, std::string("figaro_project: ") + cudaGetErrorString(e));
+  if (P.err_host[0] != FIGARO_OK) return fail(P.err_host[0], "figaro_project: singular R or Sigma");
+  return FIGARO_OK;
+}
+
 int figaro_pca_centered(figaro_plan_t p, int32_t k, double* components, double* eigvals) {
   using namespace fig;
   g_last_error.clear();

@@ -24,21 +24,6 @@ namespace fig {
 // One block.  M = R Rbar^T, S = copyltu(M), X = R^-1 S, W = (R^-1 X^T)^T, with the
 // triangular solves right-looking (row i final, then the rows above updated).  A zero
 // diagonal of R sets FIGARO_ERR_SINGULAR.  T1, T2: N x N work arrays.
-__device__ void tri_solve_upper_rows(const double* R, int64_t ldr, double* X, int N) {
-  // X <- R^-1 X for upper-triangular R (X row-major N x N), all columns at once
-  const int t = threadIdx.x, nt = blockDim.x;
-  for (int i = N - 1; i >= 0; --i) {
-    const double ri = 1.0 / R[(int64_t)i * ldr + i];
-    for (int c = t; c < N; c += nt) X[(int64_t)i * N + c] *= ri;
-    __syncthreads();
-    for (int64_t idx = t; idx < (int64_t)i * N; idx += nt) {
-      const int i2 = (int)(idx / N), c = (int)(idx % N);
-      X[(int64_t)i2 * N + c] = fma(-R[(int64_t)i2 * ldr + i], X[(int64_t)i * N + c], X[(int64_t)i2 * N + c]);
-    }
-    __syncthreads();
-  }
-}
-
 __global__ void __launch_bounds__(1024) k_grad_w(const double* R, int64_t ldr, const double* Rbar, int64_t ldb,
                                                  int N, double* W, double* T1, double* T2, int* err) {
   __shared__ int bad;

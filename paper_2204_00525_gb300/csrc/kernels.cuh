@@ -283,4 +283,47 @@ void grad_up(const GradNode& g, int64_t bound, cudaStream_t st);
 void grad_down(const GradNode& g, int j, double* dn_child, int64_t ld_child, int64_t bound, cudaStream_t st);
 void grad_rows(const GradNode& g, int64_t bound, cudaStream_t st);
 
+// ------------------------------------------------------------------ shared device helpers
+// X <- R^-1 X for upper-triangular R (row-major, ld ldr) and a row-major N x N X, by one
+// block: row i is final after its division, then the rows above lose R[i2][i] times it.
+__device__ inline void tri_solve_upper_rows(const double* R, int64_t ldr, double* X, int N) {
+  // X <- R^-1 X for upper-triangular R (X row-major N x N), all columns at once
+  const int t = threadIdx.x, nt = blockDim.x;
+  for (int i = N - 1; i >= 0; --i) {
+    const double ri = 1.0 / R[(int64_t)i * ldr + i];
+    for (int c = t; c < N; c += nt) X[(int64_t)i * N + c] *= ri;
+    __syncthreads();
+    for (int64_t idx = t; idx < (int64_t)i * N; idx += nt) {
+      const int i2 = (int)(idx / N), c = (int)(idx % N);
+      X[(int64_t)i2 * N + c] = fma(-R[(int64_t)i2 * ldr + i], X[(int64_t)i * N + c], X[(int64_t)i2 * N + c]);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ proj.cu
+constexpr int kMaxRel = 32;       // relations a projection can enumerate
+
+struct ProjNode {
+  int n_child;
+  int child[kMaxChildren];   // positions of the children in the node array
+  int64_t M;
+  const int32_t* sizes;
+  const int32_t* goff;
+  const int32_t* pgoff;
+  const uint64_t* theta;       // Theta_down per group
+  const uint64_t* theta_incl;  // its inclusive prefix over the groups
+  const uint64_t* phid;        // Phi_down per X_p group
+  const int32_t* q;            // [child][M]
+  const int32_t* perm;
+  const double* P;             // [input row][k] projected rows, or null (no data columns)
+};
+
+void tri_inverse(const double* R, int64_t ldr, int N, double* X, int* err, cudaStream_t st);
+void scale_v(const double* V, const double* sigma, int N, int k, bool divide, double* X, int* err, cudaStream_t st);
+void proj_rows(const double* data, int64_t rs, int64_t cs, int64_t M, int Ni, const double* X, int64_t ldx,
+               int col_off, int k, double* P, cudaStream_t st);
+void project(const ProjNode* nodes, int r, int k, uint64_t total, double* out, int64_t ldo, cudaStream_t st);
+
 }  // namespace fig
+
