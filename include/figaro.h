@@ -173,6 +173,14 @@ int figaro_svd(figaro_plan_t plan, double* sigma, double* V, double* R);
  * 1 <= k <= N. */
 int figaro_pca(figaro_plan_t plan, int32_t k, double* components, double* eigvals);
 
+/* Asynchronous figaro_qr_r: enqueues the same work (with host memory: the input copies,
+ * the pipeline and the copy of R back, which needs pinned R) on the plan's stream and
+ * returns; figaro_plan_sync waits for it and reports its status.  The inputs and R must
+ * stay untouched until then.  Two plans on different streams can overlap one call's
+ * transfers with the other's computation.                                              */
+int figaro_qr_r_async(figaro_plan_t plan, double* R, int64_t ldr);
+int figaro_plan_sync(figaro_plan_t plan);
+
 /* Projections of the join matrix, A X (§8.1-8.3 express Q = A R^-1, U = A V Sigma^-1 and
  * the principal-component scores A V_k through R and its SVD), at the data of the last
  * figaro_qr_r / figaro_svd / figaro_pca call; their row count is the join size, so they

@@ -87,6 +87,8 @@ def load(build_if_missing: bool = False):
         "figaro_svd_from_r_static": (C.c_int, [P, C.c_int64, C.c_int32, P, P, P]),
         "figaro_backward": (C.c_int, [P, P, C.c_int64, P, C.c_int64, P, P]),
         "figaro_pca_centered": (C.c_int, [P, C.c_int32, P, P]),
+        "figaro_qr_r_async": (C.c_int, [P, P, C.c_int64]),
+        "figaro_plan_sync": (C.c_int, [P]),
         "figaro_join_size": (C.c_int, [P, C.POINTER(C.c_uint64)]),
         "figaro_project": (C.c_int, [P, C.c_int32, P, C.c_int64, P, C.c_int64, C.c_int32, P, C.c_int64, C.c_int64,
                                      C.POINTER(C.c_int64)]),
@@ -260,6 +262,14 @@ class JoinPlan:
         R = self._out(self.n_cols, self.n_cols) if out is None else out
         figaro_qr_r(self.handle, R.data_ptr(), R.stride(0))
         return R
+
+    def qr_r_async(self, out):
+        """Enqueue a figaro_qr_r into `out` and return at once (see figaro_plan_sync)."""
+        check(load().figaro_qr_r_async(self.handle, C.c_void_p(out.data_ptr()), out.stride(0)))
+        return out
+
+    def sync(self):
+        check(load().figaro_plan_sync(self.handle))
 
     def svd(self, with_r=False):
         N = self.n_cols

@@ -131,6 +131,7 @@ struct figaro_plan_s {
   double* colsum = nullptr;            // centred PCA: column sums of A, |J|, scatter matrix
   unsigned long long* jsize = nullptr;
   double* scatter = nullptr;
+  bool pending = false;                // figaro_qr_r_async issued, figaro_plan_sync not yet
 };
 
 struct figaro_batch_s {
@@ -1169,6 +1170,30 @@ int figaro_qr_r(figaro_plan_t p, double* R, int64_t ldr) {
   if (host)
     FIG_CUDA(cudaMemcpy2DAsync(R, ldr * sizeof(double), Rd, ld * sizeof(double), p->N * sizeof(double), p->N,
                                cudaMemcpyDeviceToHost, p->st));
+  return finish(*p, 7);
+}
+
+int figaro_qr_r_async(figaro_plan_t p, double* R, int64_t ldr) {
+  g_last_error.clear();
+  if (!p || !R) return fail(FIGARO_ERR_INVALID_ARG, "null plan or R");
+  if (ldr < p->N) return fail(FIGARO_ERR_INVALID_ARG, "ldr < N");
+  const bool host = p->opt.mem == FIGARO_MEM_HOST;
+  double* Rd = host ? p->Rtmp : R;
+  int64_t ld = host ? p->N : ldr;
+  int rc = run_r(*p, Rd, ld);
+  if (rc != FIGARO_OK) return rc;
+  if (host)
+    FIG_CUDA(cudaMemcpy2DAsync(R, ldr * sizeof(double), Rd, ld * sizeof(double), p->N * sizeof(double), p->N,
+                               cudaMemcpyDeviceToHost, p->st));
+  p->pending = true;
+  return FIGARO_OK;
+}
+
+int figaro_plan_sync(figaro_plan_t p) {
+  g_last_error.clear();
+  if (!p) return fail(FIGARO_ERR_INVALID_ARG, "null plan");
+  if (!p->pending) return FIGARO_OK;
+  p->pending = false;
   return finish(*p, 7);
 }
 

@@ -440,3 +440,24 @@ def test_centered_pca(name):
         gap = (lam[j - 1] - lam[j]) / lam[0] if j < len(lam) else 1.0
         if gap > 1e-6:
             assert np.linalg.norm(comp[:, :j] @ comp[:, :j].T - W[:, :j] @ W[:, :j].T) < 1e-10 / gap + 1e-9
+
+
+def test_async_calls_on_two_plans():
+    """figaro_qr_r_async / figaro_plan_sync: two plans on two streams, host inputs, calls
+    interleaved as a pipelined user would; every R equals the synchronous call's."""
+    from paper_2204_00525_gb300 import binding
+    db = synth.path3(rows=20_000, keys=200)
+    R_ref = gpu_r(db)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    plans = [binding.plan_from_db(db, device="cpu", stream=s) for s in streams]
+    outs = [torch.empty(db.n_cols, db.n_cols, dtype=torch.float64).pin_memory() for _ in plans]
+    for i in range(6):
+        p = plans[i % 2]
+        if i >= 2:
+            p.sync()
+            assert np.array_equal(outs[i % 2].numpy(), R_ref)
+        p.qr_r_async(outs[i % 2])
+    for p, o in zip(plans, outs):
+        p.sync()
+        assert np.array_equal(o.numpy(), R_ref)
+        p.close()
