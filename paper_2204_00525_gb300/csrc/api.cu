@@ -1554,6 +1554,8 @@ int figaro_backward(figaro_plan_t p, const double* R, int64_t ldr, const double*
     g.data = n.data;
     g.rs = n.layout == FIGARO_COL_MAJOR ? 1 : n.ld;
     g.cs = n.layout == FIGARO_COL_MAJOR ? n.ld : 1;
+    g.sdata = n.b.sperm ? n.b.sdata : nullptr;      // written by the forward whenever it sorted
+    g.lds = n.b.lds;
     g.grad = grads[i];
     g.ldg = ldg[i];
     return g;

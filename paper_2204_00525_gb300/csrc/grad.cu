@@ -20,6 +20,8 @@
 
 namespace fig {
 
+constexpr int kGradChunk = 8;     // gradient columns formed together per pass
+
 // ------------------------------------------------------------------ W
 // One block.  M = R Rbar^T, S = copyltu(M), X = R^-1 S, W = (R^-1 X^T)^T, with the
 // triangular solves right-looking (row i final, then the rows above updated).  A zero
@@ -131,6 +133,22 @@ __device__ __forceinline__ void warp_add_f64(double* base, int32_t idx, double v
   if (live && lane == __ffs(peers) - 1) atomicAdd(base + idx, s);
 }
 
+// Same for non-decreasing idx across the lanes (runs of equal idx are contiguous): a
+// segmented inclusive scan, and the last lane of every run adds.
+__device__ __forceinline__ void warp_add_sorted_f64(double* base, int32_t idx, double v, bool on) {
+  const int lane = threadIdx.x & 31;
+  const int32_t key = on ? idx : -1 - lane;
+  double s = on ? v : 0.0;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double so = __shfl_up_sync(0xffffffffu, s, o);
+    const int32_t ko = __shfl_up_sync(0xffffffffu, key, o);
+    if (lane >= o && ko == key) s += so;
+  }
+  const int32_t next = __shfl_down_sync(0xffffffffu, key, 1);
+  if (on && (lane == 31 || next != key) && s != 0.0) atomicAdd(base + idx, s);
+}
+
 __global__ void k_grad_clear(double* a, int64_t ld, const int32_t* sizes, int N) {
   const int64_t P = sizes[1];
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P * N; k += (int64_t)gridDim.x * blockDim.x)
@@ -155,7 +173,7 @@ __global__ void k_grad_up(GradNode g) {
       v = group_message(g, (int32_t)grp, col, -1, 1.0, true, cu);
       target = g.g2p[grp];
     }
-    warp_add_f64(g.up + (int64_t)col * g.ldu, target, v, on);
+    warp_add_sorted_f64(g.up + (int64_t)col * g.ldu, target, v, on);   // groups are sorted by X_p
   }
 }
 
@@ -185,43 +203,63 @@ __global__ void k_grad_down(GradNode g, int j, double* dn_child, int64_t ld_chil
 }
 
 // phi(g)[a] = sum over the columns outside Y_k of m(g)[col] W[col][col_off + a]: the
-// part of the gradient shared by all tuples of group g.  Warp per group, lane per a.
+// part of the gradient shared by all tuples of group g.  Thread per group: m(g) column by
+// column, accumulated into kGradChunk outputs at a time (no cross-lane sums: every FP64
+// instruction does useful work in every lane).
 __global__ void k_grad_group(GradNode g) {
   const int64_t G = g.sizes[0];
-  const int lane = threadIdx.x & 31;
-  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t grp = w0; grp < G; grp += nw) {
+  for (int64_t grp = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; grp < G;
+       grp += (int64_t)gridDim.x * blockDim.x) {
     double cu[kMaxChildren];
     for (int c = 0; c < g.n_child; ++c) cu[c] = child_count(g, c, (int32_t)grp);
     const double cd = g.is_root ? 1.0 : (double)g.phiu[g.g2p[grp]];
-    for (int a0 = 0; a0 < g.Ni; a0 += 32) {
-      const int a = a0 + lane;
-      double s = 0.0;
+    for (int a0 = 0; a0 < g.Ni; a0 += kGradChunk) {
+      double acc[kGradChunk];
+#pragma unroll
+      for (int q = 0; q < kGradChunk; ++q) acc[q] = 0.0;
       for (int col = 0; col < g.N; ++col) {
         if (g.colkind[col] == 0) continue;
         const double m = group_message(g, (int32_t)grp, col, -1, cd, false, cu, true);
-        if (m != 0.0 && a < g.Ni) s = fma(m, g.W[(int64_t)col * g.N + g.col_off + a], s);
+        if (m == 0.0) continue;
+        const double* wrow = g.W + (int64_t)col * g.N + g.col_off + a0;
+#pragma unroll
+        for (int q = 0; q < kGradChunk; ++q)
+          if (a0 + q < g.Ni) acc[q] = fma(m, wrow[q], acc[q]);
       }
-      if (a < g.Ni) g.phi[(int64_t)a * g.M + grp] = s;
+#pragma unroll
+      for (int q = 0; q < kGradChunk; ++q)
+        if (a0 + q < g.Ni) g.phi[(int64_t)(a0 + q) * g.M + grp] = acc[q];
     }
   }
 }
 
 // dL/dy_t[a] = Phi_circ(g) sum_b y_t[b] W[col_off + b][col_off + a] + phi(g)[a], written at
-// the tuple's input row.  Thread per (sorted row, column a).
+// the tuple's input row.  Thread per sorted row: its values come from the sorted copy of
+// the data that the forward pass kept (coalesced), all its columns at once.
 __global__ void k_grad_rows(GradNode g) {
-  const int a = blockIdx.y;
   const int64_t M = g.M;
   const double* Wk = g.W + (int64_t)g.col_off * g.N + g.col_off;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < M; e += (int64_t)gridDim.x * blockDim.x) {
     const int32_t grp = g.row_gid[e];
     const int64_t src = g.perm ? g.perm[e] : e;
     const double c = (double)g.phic[grp];
-    double s = 0.0;
-    if (c != 0.0)
-      for (int b = 0; b < g.Ni; ++b) s = fma(g.data[src * g.rs + (int64_t)b * g.cs], Wk[(int64_t)b * g.N + a], s);
-    g.grad[(int64_t)a * g.ldg + src] = fma(c, s, g.phi[(int64_t)a * g.M + grp]);
+    for (int a0 = 0; a0 < g.Ni; a0 += kGradChunk) {
+      double s[kGradChunk];
+#pragma unroll
+      for (int q = 0; q < kGradChunk; ++q) s[q] = 0.0;
+      if (c != 0.0)
+        for (int b = 0; b < g.Ni; ++b) {
+          const double y = g.sdata ? g.sdata[(int64_t)b * g.lds + e] : g.data[src * g.rs + (int64_t)b * g.cs];
+          const double* wrow = Wk + (int64_t)b * g.N + a0;
+#pragma unroll
+          for (int q = 0; q < kGradChunk; ++q)
+            if (a0 + q < g.Ni) s[q] = fma(y, wrow[q], s[q]);
+        }
+#pragma unroll
+      for (int q = 0; q < kGradChunk; ++q)
+        if (a0 + q < g.Ni)
+          g.grad[(int64_t)(a0 + q) * g.ldg + src] = fma(c, s[q], g.phi[(int64_t)(a0 + q) * g.M + grp]);
+    }
   }
 }
 
@@ -244,8 +282,8 @@ void grad_down(const GradNode& g, int j, double* dn_child, int64_t ld_child, int
 
 void grad_rows(const GradNode& g, int64_t bound, cudaStream_t st) {
   if (g.Ni == 0) return;
-  k_grad_group<<<grid_for(bound * 32, 256, 152 * 16), 256, 0, st>>>(g);
-  k_grad_rows<<<dim3(grid_for(bound, 256, 152 * 8), g.Ni), 256, 0, st>>>(g);
+  k_grad_group<<<grid_for(bound, 256, 152 * 8), 256, 0, st>>>(g);
+  k_grad_rows<<<grid_for(bound, 256, 152 * 8), 256, 0, st>>>(g);
 }
 
 }  // namespace fig

@@ -272,6 +272,8 @@ struct GradNode {
   double* phi;               // [a][g], ld M
   const double* data;        // the relation's data: element (row r, column b) at r * rs + b * cs
   int64_t rs, cs;
+  const double* sdata;       // the forward's copy of the data in sorted order (or null), ld lds
+  int64_t lds;
   double* grad;              // output, column-major, ld ldg (input row order)
   int64_t ldg;
 };
