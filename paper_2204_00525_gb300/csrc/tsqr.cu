@@ -102,7 +102,7 @@ __device__ void hh_small(E* A, int lda, int m, int n, E* red) {
       const E dj = part[lane] + part[32 + lane];
       const E sigma = __shfl_sync(0xffffffffu, dj, 0);
       E wj = 0;
-      if (sigma != E(0)) {                       // warp-uniform
+      if (!f64_is_zero(sigma)) {                 // warp-uniform
         const E alpha = ak[k];
         const bool mine = j < n && lane > 0;
         E* aj = A + (int64_t)(mine ? j : k) * lda;

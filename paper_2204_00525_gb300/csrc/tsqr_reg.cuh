@@ -54,11 +54,37 @@ struct HhScalars {
 // square root and the reciprocal are formed by Newton-Raphson iterations from float
 // hardware approximations (relative error below 2^-22): y <- y (3/2 - t y^2 / 2) for
 // 1 / sqrt(t) and r <- r (2 - d r) for 1 / d, two steps each (quadratic convergence; a
-// measured sweep gives at most 4e-16 relative error for nu and 1e-15 for tau).  Outside
-// the range where the float seeds are accurate the plain operations are used.
+// measured sweep gives at most 4e-16 relative error for nu and 1e-15 for tau).  The
+// float seeds are moved between the formats by exponent arithmetic on the bit patterns
+// (conversions, comparisons and sign tests would each take an FP64 issue slot), which
+// is exact for the normal values of the range tested first; outside it (|t| beyond
+// 2^+-100) the plain operations are used.
 static __device__ __noinline__ void hh_scalars_wide(double alpha, double sigma, double& nu, double& tau) {
   nu = sqrt(fma(alpha, alpha, sigma));
   tau = 1.0 / (nu * (nu + fabs(alpha)));
+}
+
+// float nearest below a positive normal double whose exponent is within float range
+__device__ __forceinline__ float f32_of_f64_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32);
+  const unsigned e = (hi >> 20) & 0x7FFu;
+  const unsigned mant = ((hi & 0xFFFFFu) << 3) | (unsigned)((b >> 29) & 7ull);
+  return __uint_as_float(((e - 1023u + 127u) << 23) | mant);
+}
+
+// the double equal to a positive normal float
+__device__ __forceinline__ double f64_of_f32_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long e = (u >> 23) & 0xFFu;
+  const unsigned long long m = u & 0x7FFFFFu;
+  return __longlong_as_double((long long)(((e - 127ull + 1023ull) << 52) | (m << 29)));
+}
+
+// |x| in [2^-100, 2^100), by the exponent field
+__device__ __forceinline__ bool f64_mid_range(double x) {
+  const unsigned e = ((unsigned)((unsigned long long)__double_as_longlong(x) >> 52)) & 0x7FFu;
+  return e >= 1023u - 100u && e < 1023u + 100u;
 }
 
 template <>
@@ -66,23 +92,27 @@ struct HhScalars<double> {
   __device__ static void get(double alpha, double sigma, double& beta, double& v0, double& tau) {
     const double t = fma(alpha, alpha, sigma);
     double nu;
-    if (t > 1e-30 && t < 1e30) {
-      double y = (double)rsqrtf((float)t);
+    if (f64_mid_range(t)) {
+      double y = f64_of_f32_bits(rsqrtf(f32_of_f64_bits(t)));
       const double ht = 0.5 * t;
       y = y * fma(-ht * y, y, 1.5);
       y = y * fma(-ht * y, y, 1.5);
       nu = t * y;
       const double d = nu * (nu + fabs(alpha));
-      double r = (double)__frcp_rn((float)d);
+      double r = f64_of_f32_bits(__frcp_rn(f32_of_f64_bits(d)));
       r = r * fma(-d, r, 2.0);
       tau = r * fma(-d, r, 2.0);
     } else {
       hh_scalars_wide(alpha, sigma, nu, tau);
     }
-    beta = alpha >= 0.0 ? -nu : nu;
+    beta = __double_as_longlong(alpha) >= 0 ? -nu : nu;     // sign bit: no FP64 compare
     v0 = alpha - beta;
   }
 };
+
+// x == 0 (either sign) without an FP64 compare
+__device__ __forceinline__ bool f64_is_zero(double x) { return ((unsigned long long)__double_as_longlong(x) << 1) == 0ull; }
+__device__ __forceinline__ bool f64_is_zero(float x) { return x == 0.0f; }
 
 // ------------------------------------------------------------------ multi-value warp sum
 // Sum NW per-lane values over the warp by recursive halving: at the level with lane
@@ -169,7 +199,7 @@ __device__ __forceinline__ void reg_hh_step(E (&a)[RPL][N], int m, int lane) {
     for (int t = 0; t < C; ++t) d[t] = fma(x[r], a[r][K + t], d[t]);
   const E mine = warp_multi_sum<E, P2>(d, lane);
   const E sig = __shfl_sync(0xffffffffu, mine, lane_of_value<P2>(0));
-  if (sig == E(0)) return;                   // uniform: column already reduced below K
+  if (f64_is_zero(sig)) return;              // uniform: column already reduced below K
   constexpr int kr = K / 32, kl = K % 32;    // lane and slot holding row K
   const E alpha = __shfl_sync(0xffffffffu, a[kr][K], kl);
   E beta, v0, tau;
