@@ -56,6 +56,7 @@ enum figaro_status {
 enum { FIGARO_KEY_I64 = 0, FIGARO_KEY_I32 = 1 };
 enum { FIGARO_COL_MAJOR = 0, FIGARO_ROW_MAJOR = 1 };
 enum { FIGARO_PREC_FP64 = 0, FIGARO_PREC_MIXED = 1, FIGARO_PREC_MIXED_REFINED = 2 };
+enum { FIGARO_LEAF_HOUSEHOLDER = 0, FIGARO_LEAF_GIVENS = 1 };
 enum { FIGARO_MEM_DEVICE = 0, FIGARO_MEM_HOST = 1 };
 
 /* One relation S_i (§2 "Relations and Joins").
@@ -112,7 +113,12 @@ typedef struct figaro_join_tree {
  *                    tuples are given weight 0, which is exact since they are not in A.
  *   mem              FIGARO_MEM_DEVICE or FIGARO_MEM_HOST (see the conventions).
  *   stage_timing     1: time every stage with CUDA events (figaro_stage_times).
- *   gradients        1: also hold the workspace of figaro_backward (device memory only). */
+ *   gradients        1: also hold the workspace of figaro_backward (device memory only).
+ *   leaf             FIGARO_LEAF_HOUSEHOLDER (default) or FIGARO_LEAF_GIVENS: TSQR leaves
+ *                    of blocks with <= 16 columns by per-thread Givens rotations on
+ *                    32-row chunks, skipping exact zeros (the paper's THIN flavour, for
+ *                    very sparse blocks; wider blocks keep Householder), in float64 on
+ *                    both precisions.                                                  */
 typedef struct figaro_options {
   int32_t precision;
   int32_t presorted;
@@ -120,7 +126,8 @@ typedef struct figaro_options {
   int32_t mem;
   int32_t stage_timing;
   int32_t gradients;
-  int32_t reserved[10];
+  int32_t leaf;
+  int32_t reserved[9];
 } figaro_options;
 
 typedef struct figaro_plan_s* figaro_plan_t;

@@ -20,6 +20,7 @@ FIGARO_KEY_I64, FIGARO_KEY_I32 = 0, 1
 FIGARO_COL_MAJOR, FIGARO_ROW_MAJOR = 0, 1
 FIGARO_PREC_FP64, FIGARO_PREC_MIXED, FIGARO_PREC_MIXED_REFINED = 0, 1, 2
 FIGARO_PROJ_X, FIGARO_PROJ_Q, FIGARO_PROJ_U, FIGARO_PROJ_SCORES = 0, 1, 2, 3
+FIGARO_LEAF_HOUSEHOLDER, FIGARO_LEAF_GIVENS = 0, 1
 FIGARO_MEM_DEVICE, FIGARO_MEM_HOST = 0, 1
 DBG = {"sizes": 0, "perm": 1, "group_off": 2, "counts": 3, "pcounts": 4, "tails": 5, "heads": 6,
        "gen_tails": 7, "data": 8, "root_rows": 9}
@@ -41,7 +42,7 @@ class figaro_join_tree(C.Structure):
 class figaro_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("presorted", C.c_int32), ("require_reduced", C.c_int32),
                 ("mem", C.c_int32), ("stage_timing", C.c_int32), ("gradients", C.c_int32),
-                ("reserved", C.c_int32 * 10)]
+                ("leaf", C.c_int32), ("reserved", C.c_int32 * 9)]
 
 
 class figaro_plan_info(C.Structure):
@@ -211,7 +212,7 @@ class JoinPlan:
 
     def __init__(self, relations, parent, precision=FIGARO_PREC_FP64, presorted=False,
                  require_reduced=False, mem=FIGARO_MEM_DEVICE, stage_timing=False, stream=None,
-                 gradients=False):
+                 gradients=False, leaf=FIGARO_LEAF_HOUSEHOLDER):
         import torch
         self._keep = []
         self._data = []
@@ -247,6 +248,7 @@ class JoinPlan:
         opt.mem = mem
         opt.stage_timing = int(stage_timing)
         opt.gradients = int(gradients)
+        opt.leaf = int(leaf)
         self.mem = mem
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.handle = figaro_plan(tree, opt, self.stream.cuda_stream)

@@ -532,7 +532,7 @@ static void make_blocks(figaro_plan_s& P) {
       t.kind = BLK_TAILS;
       t.M = n.M;
       t.bound = n.M;
-      tsqr_plan_block(t, mixed);
+      tsqr_plan_block(t, mixed, P.opt.leaf == FIGARO_LEAF_GIVENS);
       P.blocks.push_back(t);
       P.stack_rows += t.n;
     }
@@ -544,7 +544,7 @@ static void make_blocks(figaro_plan_s& P) {
       t.prio = true;
       t.M = n.M;
       t.bound = n.M;
-      tsqr_plan_block(t, mixed);
+      tsqr_plan_block(t, mixed, P.opt.leaf == FIGARO_LEAF_GIVENS);
       P.blocks.push_back(t);
       P.stack_rows += t.n;
     }
@@ -556,7 +556,7 @@ static void make_blocks(figaro_plan_s& P) {
       t.prio = true;
       t.M = n.M;
       t.bound = n.M;
-      tsqr_plan_block(t, mixed);
+      tsqr_plan_block(t, mixed, P.opt.leaf == FIGARO_LEAF_GIVENS);
       P.blocks.push_back(t);
       P.stack_rows += t.n;
     }
@@ -1042,8 +1042,9 @@ int figaro_plan(const figaro_join_tree* tree, const figaro_options* opt, void* s
   auto* P = new (std::nothrow) figaro_plan_s();
   if (!P) return fail(FIGARO_ERR_NOMEM, "host allocation");
   if (opt) P->opt = *opt; else figaro_default_options(&P->opt);
-  if (P->opt.precision != FIGARO_PREC_FP64 && P->opt.precision != FIGARO_PREC_MIXED &&
-      P->opt.precision != FIGARO_PREC_MIXED_REFINED) {
+  if ((P->opt.precision != FIGARO_PREC_FP64 && P->opt.precision != FIGARO_PREC_MIXED &&
+       P->opt.precision != FIGARO_PREC_MIXED_REFINED) ||
+      (P->opt.leaf != FIGARO_LEAF_HOUSEHOLDER && P->opt.leaf != FIGARO_LEAF_GIVENS)) {
     delete P;
     return fail(FIGARO_ERR_INVALID_ARG, "precision");
   }

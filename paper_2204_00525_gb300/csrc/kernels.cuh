@@ -209,11 +209,12 @@ struct TsqrBlock {
   int nreg;                  // register (warp-per-tile) path: padded column count; 0 = not used
   int64_t warp_min;          // register path: levels with at least this many tiles (else block-per-tile)
   bool prio;                 // on the critical path: its stream gets the high priority
+  bool givens;               // leaf by per-thread Givens rotations on b.tile-row chunks
   const int* cols;           // device [n]: global column of each block column
   void* scratch;             // block path: global tile slots when a tile exceeds shared memory
 };
 
-void tsqr_plan_block(TsqrBlock& b, bool mixed);
+void tsqr_plan_block(TsqrBlock& b, bool mixed, bool givens = false);
 int64_t tsqr_tri_elems(const TsqrBlock& b);
 int64_t tsqr_scratch_elems(const TsqrBlock& b, bool mixed);
 void tsqr_leaf(const TsqrBlock& b, bool mixed, cudaStream_t st, int64_t* launches);

@@ -24,6 +24,7 @@ namespace fig {
 
 constexpr int kQrThreads = 256;   // 8 warps: hh_small's row classes
 constexpr int kRedElems = 320;     // reduction scratch ahead of the tile in shared memory
+constexpr int kGivensRows = 32;    // rows per thread of the Givens leaf
 constexpr size_t kSmemCap = 200 * 1024;
 
 // ------------------------------------------------------------------ block path (n > 32)
@@ -186,6 +187,68 @@ __global__ void __launch_bounds__(kQrThreads) k_tsqr_cta(TsqrBlock b, const doub
   }
 }
 
+// ------------------------------------------------------------------ Givens leaf (option)
+// The paper's THIN post-processing (§7, after Golub et al.) gives each thread a share of
+// a block's rows, which it brings to upper-triangular form by Givens rotations, and then
+// combines the threads' triangles.  Here one thread per chunk of kGivensRows rows keeps an
+// n x n triangle and rotates every row into it, column by column: rotation (c, s) with
+// r = sqrt(T_kk^2 + x_k^2), c = T_kk / r, s = x_k / r turns (T_kj, x_j) into
+// (c T_kj + s x_j, -s T_kj + c x_j).  A row entry that is exactly zero needs no rotation
+// and is skipped, which is what makes this leaf pay on very sparse blocks (as is an entry
+// whose square underflows together with T_kk's, at an error below the format's smallest
+// normal); the chunk triangles then go through the same TSQR tree as the Householder
+// leaves.
+template <typename E, int NMAX>
+__global__ void __launch_bounds__(128) k_tsqr_givens(TsqrBlock b, double* tri_out) {
+  const int n = b.n;
+  const int64_t rows = block_rows(b);
+  const int64_t tiles = (rows + kGivensRows - 1) / kGivensRows;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tiles; t += (int64_t)gridDim.x * blockDim.x) {
+    E T[NMAX][NMAX];
+#pragma unroll
+    for (int i = 0; i < NMAX; ++i)
+#pragma unroll
+      for (int j = 0; j < NMAX; ++j) T[i][j] = E(0);
+    const int64_t r0 = t * kGivensRows;
+    const int m = (int)(rows - r0 < kGivensRows ? rows - r0 : kGivensRows);
+    for (int i = 0; i < m; ++i) {
+      E x[NMAX];
+#pragma unroll
+      for (int c = 0; c < NMAX; ++c)
+        x[c] = c < n ? (b.ptr32 ? (E)b.ptr32[(int64_t)c * b.ld + r0 + i] : (E)b.ptr[(int64_t)c * b.ld + r0 + i]) : E(0);
+#pragma unroll
+      for (int k = 0; k < NMAX; ++k) {
+        if (x[k] == E(0)) continue;                   // nothing to rotate away
+        const E a = T[k][k];
+        const E r = sqrt(fma(a, a, x[k] * x[k]));
+        if (r == E(0)) continue;                      // both below the square's underflow
+        const E c = a / r, s = x[k] / r;
+        T[k][k] = r;
+#pragma unroll
+        for (int j = k + 1; j < NMAX; ++j) {
+          const E tj = T[k][j];
+          T[k][j] = fma(c, tj, s * x[j]);
+          x[j] = fma(-s, tj, c * x[j]);
+        }
+      }
+    }
+    double* tri = tri_out + t * n * n;
+#pragma unroll
+    for (int c = 0; c < NMAX; ++c)
+#pragma unroll
+      for (int r = 0; r < NMAX; ++r)
+        if (c < n && r < n) tri[(int64_t)c * n + r] = r <= c ? (double)T[r][c] : 0.0;   // T is exact
+  }
+}
+
+template <typename E>
+static void launch_givens(const TsqrBlock& b, cudaStream_t st) {
+  const int64_t tiles = (b.bound + kGivensRows - 1) / kGivensRows;
+  const unsigned grid = grid_for(tiles, 128, 152 * 16);
+  if (b.nreg <= 8) k_tsqr_givens<E, 8><<<grid, 128, 0, st>>>(b, b.tri[0]);
+  else k_tsqr_givens<E, 16><<<grid, 128, 0, st>>>(b, b.tri[0]);
+}
+
 // ------------------------------------------------------------------ final stack and R
 // One thread block places every block's triangle at its global columns: stack rows
 // [off_b, off_b + n_b), column-major with leading dimension stack_rows.
@@ -238,10 +301,11 @@ static int reg_tile_of(int N) {
 
 static size_t cta_smem(int lda, int n, size_t esz) { return (kRedElems + (size_t)lda * n) * esz; }
 
-void tsqr_plan_block(TsqrBlock& b, bool mixed) {
+void tsqr_plan_block(TsqrBlock& b, bool mixed, bool givens) {
   const int n = b.n;
   const size_t esz = mixed ? sizeof(float) : sizeof(double);
   b.nreg = reg_class(n);
+  b.givens = givens && b.nreg && b.nreg <= 16;
   if (b.nreg) {
     // one warp's QR of a tile costs about N^2 FP64 instructions at ~70 cycles each: for
     // N <= 16 (tiles of 128-256 rows) it beats a thread block per tile from two tiles
@@ -251,6 +315,7 @@ void tsqr_plan_block(TsqrBlock& b, bool mixed) {
     // n <= 16: tree tiles fill a register tile (fan = TW / n >= 4); wider blocks reduce
     // their trees with the block-per-tile kernel only, six triangles at a time
     b.fan = b.nreg <= 16 ? b.tile / n : 6;
+    if (b.givens) b.tile = kGivensRows;       // leaf chunks of the Givens leaf
   } else {
     b.warp_min = 0;
     int64_t t = (int64_t)(64 * 1024 / (esz * n));
@@ -320,6 +385,14 @@ void tsqr_leaf(const TsqrBlock& b, bool mixed, cudaStream_t st, int64_t* launche
   void* scratch = b.scratch;
   const int64_t tiles = (b.bound + b.tile - 1) / b.tile;
   if (tiles < 1) return;
+  if (b.givens) {
+    // float64 on both paths: rotated in float, the chunk triangles of very sparse
+    // blocks lose up to 2e-5 of R^T R (measured), far above the float Householder leaf
+    launch_givens<double>(b, st);
+    (void)mixed;
+    ++*launches;
+    return;
+  }
   if (b.nreg) {
     if (mixed) {
       launch_reg_n<float>(b, nullptr, b.tri[0], 0, tiles, st);
