@@ -41,8 +41,8 @@ SAMPLE_ROWS = 100_000          # oracle sample per relation (same shape and key 
 FP64_PEAK_TFLOPS = 152 * 2070e6 * 4 / 1e12   # 152 SMs x 2.07 GHz x 2 DFMA/clk/SM x 2 flop
 # DRAM bytes per input row of the dominant kernel (k_tsqr_reg<double, 8>, leaf of a tails
 # block), from the ncu capture summarised in profiles/tsqr_reg8_fp64_path3_2m.md:
-# (dram__bytes_read.sum + dram__bytes_write.sum) / rows = 131.99 MB / 1,998,000 rows.
-DOMINANT_DRAM_BYTES_PER_ROW = 131.99e6 / 1_998_000
+# (dram__bytes_read.sum + dram__bytes_write.sum) / rows = 132.37 MB / 1,998,000 rows.
+DOMINANT_DRAM_BYTES_PER_ROW = 132.37e6 / 1_998_000
 
 
 def log(*a):
