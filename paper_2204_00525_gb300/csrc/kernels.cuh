@@ -211,7 +211,12 @@ struct TsqrBlock {
   bool prio;                 // on the critical path: its stream gets the high priority
   bool givens;               // leaf by per-thread Givens rotations on b.tile-row chunks
   const int* cols;           // device [n]: global column of each block column
-  void* scratch;             // block path: global tile slots when a tile exceeds shared memory
+  void* scratch;             // block path: global tile slots when a tile exceeds shared memory;
+                             // fold path: one n x n triangle per thread block when T is not in shared memory
+  bool fold;                 // n > 32: streamed fold (b.tile = chunk rows, b.seg chunks per leaf triangle)
+  bool fold_tsmem;           // fold path: the running triangle lives in shared memory
+  int64_t seg;               // fold path: at most this many chunks folded into one leaf triangle
+  int64_t fold_g0;           // fold path: thread blocks of the leaf launch
 };
 
 void tsqr_plan_block(TsqrBlock& b, bool mixed, bool givens = false);

@@ -249,6 +249,333 @@ static void launch_givens(const TsqrBlock& b, cudaStream_t st) {
   else k_tsqr_givens<E, 16><<<grid, 128, 0, st>>>(b, b.tri[0]);
 }
 
+// ------------------------------------------------------------------ streamed fold (n > 32)
+// A wide block is reduced by folding.  A thread block keeps one n x n triangle T, the R of
+// the rows it has folded so far, and brings every next chunk X of its rows into it column
+// by column: the reflector of column k maps (T_kk, X[:, k]) to (beta, 0) (alpha = T_kk,
+// sigma = ||X[:, k]||^2; normalised as in FoldScalars), and for every later column j
+// w_j = tau' (T_kj + X[:, k]^T X[:, j] / v0), T_kj -= w_j, X[:, j] -= (w_j / v0) X[:, k].  This is
+// Householder QR of the stacked [T; X] with the zeros of T skipped, 2 m n^2 flops per chunk
+// of m rows, so a block of M rows costs the 2 M n^2 of one tall QR and no tree work inside a
+// thread block.  The leaf gives one triangle per b.seg chunks; tree levels fold b.fan such
+// triangles each, several stacked in one chunk when they fit, skipping the rows that are
+// zero in the column being reduced (row i of an upper triangle is zero before column i),
+// (2/3) n^3 flops per triangle.
+//
+// Per column k, two passes separated by barriers.  Pass A: warps 0-7 form partial dot
+// products of column k with columns k+1.. over row slices (slice s of S takes rows s,
+// s + S, ...; thread (column, slice)) while lane 0 of warp 8 forms the scalars from the
+// norm and T_kk found in the previous pass.  Pass B: warps 0-7 sum the partials of
+// columns k+2.. and update them; warp 8 updates column k+1 and reduces its sum of
+// squares over the warp, which the next column's scalars need.
+constexpr int kFoldThreads = 288;
+constexpr int kFoldWorkers = 256;
+constexpr int kFoldPivotWarp = kFoldWorkers / 32;
+constexpr int kFoldMaxSlices = 8;
+constexpr size_t kFoldSmemF32 = 100 * 1024;   // two float blocks per SM (latency-bound)
+
+__host__ __device__ __forceinline__ int fold_red_elems(int n) {
+  const int part = n > kFoldWorkers ? n : kFoldWorkers;
+  return ((part + n + 4) + 3) & ~3;
+}
+
+// Scalars of the fold's reflector in normalised form: v' = v / v0 = (1, x / v0) and
+// tau' = tau v0^2 = |v0| / nu (in [1, 2]), returned with rv = 1 / v0.  Unlike
+// tau = 1 / (nu (nu + |alpha|)) this stays finite when sigma is far below the format's
+// smallest normal, as the rounding residue of a chunk with fewer rows than columns
+// becomes after enough reflections.
+template <typename E>
+struct FoldScalars {
+  __device__ static void get(E alpha, E sigma, E& beta, E& taup, E& rv) {
+    const E nu = sqrt(fma(alpha, alpha, sigma));
+    beta = alpha >= E(0) ? -nu : nu;
+    const E v0 = alpha - beta;
+    taup = fabs(v0) / nu;
+    rv = E(1) / v0;
+  }
+};
+
+template <>
+struct FoldScalars<double> {
+  __device__ static void get(double alpha, double sigma, double& beta, double& taup, double& rv) {
+    const double t = fma(alpha, alpha, sigma);
+    if (f64_mid_range(t)) {
+      // 1/sqrt(t) and 1/v0 by two Newton-Raphson steps each from the float approximations
+      // (as in HhScalars<double>); |v0| is in [nu, 2 nu], inside the float range with t
+      double y = f64_of_f32_bits(rsqrtf(f32_of_f64_bits(t)));
+      const double ht = 0.5 * t;
+      y = y * fma(-ht * y, y, 1.5);
+      y = y * fma(-ht * y, y, 1.5);
+      const double nu = t * y;
+      const bool neg = __double_as_longlong(alpha) < 0;
+      beta = neg ? nu : -nu;
+      const double av0 = fabs(alpha) + nu;           // |v0| = |alpha - beta|
+      taup = av0 * y;
+      double r = f64_of_f32_bits(__frcp_rn(f32_of_f64_bits(av0)));
+      r = r * fma(-av0, r, 2.0);
+      r = r * fma(-av0, r, 2.0);
+      rv = neg ? -r : r;                             // v0 has the sign of alpha
+    } else {
+      const double nu = sqrt(t);
+      beta = alpha >= 0.0 ? -nu : nu;
+      const double v0 = alpha - beta;
+      taup = fabs(v0) / nu;
+      rv = 1.0 / v0;
+    }
+  }
+};
+
+template <typename E>
+__device__ __forceinline__ E fold_warp_sum(E v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// slices for cols columns over the worker threads
+__device__ __forceinline__ int fold_slices(int cols) {
+  if (cols <= 0) return 0;
+  int S = kFoldWorkers / cols;
+  if (S > kFoldMaxSlices) S = kFoldMaxSlices;
+  return S < 1 ? 1 : S;
+}
+
+// Folds X into T.  X holds P row blocks of h rows each (row block p at rows [p h, p h + h),
+// leading dimension ldx).  Dense: every row may be non-zero.  tri: every row block holds
+// rows [r0, r0 + h) of an upper triangle, so that in column k only its first
+// k + 1 - r0 rows can be non-zero.
+template <typename E>
+__device__ void fold_chunk(E* X, int ldx, int h, int P, int n, int r0, bool tri, E* T, E* red) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  E* part = red;                                          // [S * cp] partial dots
+  E* trow = red + (n > kFoldWorkers ? n : kFoldWorkers);  // T[k][k+1..n-1] of the step
+  E* sc = trow + n;                                       // tau', 1/v0, next sigma, next alpha
+  auto rows_at = [&](int k) -> int {
+    if (!tri) return h;
+    const int r = k + 1 - r0;
+    return r < 0 ? 0 : (r > h ? h : r);
+  };
+  // a piece starting at row r0 of a triangle is zero in columns < r0: their reflectors
+  // are the identity
+  const int kbeg = tri ? (r0 < n ? r0 : n) : 0;
+  if (kbeg >= n) return;
+  if (warp == kFoldPivotWarp) {
+    const int ra = rows_at(kbeg);
+    const E* x0 = X + (int64_t)kbeg * ldx;
+    E sq = E(0);
+    for (int p = 0; p < P; ++p)
+      for (int i = lane; i < ra; i += 32) {
+        const E v = x0[p * h + i];
+        sq = fma(v, v, sq);
+      }
+    sq = fold_warp_sum(sq);
+    if (lane == 0) {
+      sc[2] = sq;
+      sc[3] = T[(int64_t)kbeg * n + kbeg];
+    }
+  }
+  __syncthreads();
+  for (int k = kbeg; k < n; ++k) {
+    const int ra = rows_at(k), rb = rows_at(k + 1);   // rows [ra, rb) have X[i][k] = 0
+    const int cp = n - 1 - k;                         // columns k+1 .. n-1
+    const int S = fold_slices(cp);
+    const E* xk = X + (int64_t)k * ldx;
+    E* trk = T + (int64_t)k * n;
+    if (tid < kFoldWorkers) {
+      const int items = S * cp;
+      for (int e = tid; e < items; e += kFoldWorkers) {
+        const int jc = e % cp, s = e / cp;
+        if (s == 0) trow[jc] = trk[k + 1 + jc];
+        const E* xj = xk + (int64_t)(jc + 1) * ldx;
+        E d0 = E(0), d1 = E(0);
+        for (int p = 0; p < P; ++p) {
+          const E* a = xk + p * h;
+          const E* c = xj + p * h;
+          int i = s;
+          for (; i + S < ra; i += 2 * S) {
+            d0 = fma(a[i], c[i], d0);
+            d1 = fma(a[i + S], c[i + S], d1);
+          }
+          if (i < ra) d0 = fma(a[i], c[i], d0);
+        }
+        part[e] = d0 + d1;
+      }
+    } else if (tid == kFoldWorkers) {
+      const E sigma = sc[2], alpha = sc[3];
+      E beta = alpha, taup = E(0), rv = E(0);           // a zero column: nothing to reflect
+      if (!f64_is_zero(sigma)) FoldScalars<E>::get(alpha, sigma, beta, taup, rv);
+      trk[k] = beta;
+      sc[0] = taup;
+      sc[1] = rv;
+    }
+    __syncthreads();
+    const E taup = sc[0], rv = sc[1];
+    if (tid < kFoldWorkers) {
+      const int cq = cp - 1;                          // columns k+2 .. n-1
+      const int S2 = fold_slices(cq);
+      const int items = S2 * cq;
+      for (int e = tid; e < items; e += kFoldWorkers) {
+        const int jc = e % cq + 1, s = e / cq;
+        E d = part[jc];
+        for (int q = 1; q < S; ++q) d += part[q * cp + jc];
+        const E tj = trow[jc];
+        const E wt = taup * fma(rv, d, tj);             // w' = tau' (T_kj + d_j / v0)
+        if (s == 0) trk[k + 1 + jc] = tj - wt;
+        const E w = wt * rv;                              // X[:, j] -= w' (X[:, k] / v0)
+        E* xj = X + (int64_t)(k + 1 + jc) * ldx;
+        for (int p = 0; p < P; ++p) {
+          const E* a = xk + p * h;
+          E* c = xj + p * h;
+          for (int i = s; i < ra; i += S2) c[i] = fma(-w, a[i], c[i]);
+        }
+      }
+    } else if (cp > 0) {
+      // warp 8: column k+1 and the sum of squares of its rows for the next step
+      const E alpha_next = lane == 0 ? T[(int64_t)(k + 1) * n + k + 1] : E(0);
+      E d = part[0];
+      for (int q = 1; q < S; ++q) d += part[q * cp];
+      const E tj = trow[0];
+      const E wt = taup * fma(rv, d, tj);
+      const E w = wt * rv;
+      E* xj = X + (int64_t)(k + 1) * ldx;
+      E sq = E(0);
+      for (int p = 0; p < P; ++p) {
+        const E* a = xk + p * h;
+        E* c = xj + p * h;
+        for (int i = lane; i < rb; i += 32) {
+          const E v = fma(-w, a[i], c[i]);
+          c[i] = v;
+          sq = fma(v, v, sq);
+        }
+      }
+      sq = fold_warp_sum(sq);
+      if (lane == 0) {
+        trk[k + 1] = tj - wt;
+        sc[2] = sq;
+        sc[3] = alpha_next;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// level 0: the leaf over the block's rows; level l > 0: tree level l over tri_in.
+template <typename E>
+__global__ void __launch_bounds__(kFoldThreads) k_tsqr_fold(TsqrBlock b, const double* tri_in, double* tri_out,
+                                                            int level) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = b.n, mc = b.tile, ldx = mc + 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  E* red = reinterpret_cast<E*>(smem_raw);
+  E* X = red + fold_red_elems(n);
+  E* T = b.fold_tsmem ? X + (int64_t)ldx * n : static_cast<E*>(b.scratch) + (int64_t)blockIdx.x * n * n;
+  const int64_t rows = block_rows(b);
+  // chunks per leaf triangle from the live rows: the leaf's thread blocks share them evenly
+  const int64_t chunks = (rows + mc - 1) / mc;
+  int64_t seg = (chunks + b.fold_g0 - 1) / b.fold_g0;
+  if (seg > b.seg) seg = b.seg;
+  if (seg < 1) seg = 1;
+  int64_t live = chunks;                      // leaf: live chunks
+  int64_t per = seg;
+  if (level > 0) {
+    live = (live + seg - 1) / seg;            // live leaf triangles
+    for (int l = 1; l < level; ++l) live = (live + b.fan - 1) / b.fan;
+    per = b.fan;
+    if (live == 1) {                          // one triangle: copied
+      if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < n * n; i += blockDim.x) tri_out[i] = tri_in[i];
+      return;
+    }
+  }
+  const int stack = mc / n;                   // whole triangles per chunk on tree levels
+  int64_t units = (live + per - 1) / per;
+  if (units < 1) units = 1;                   // an empty block still leaves a (zero) triangle
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) T[i] = E(0);
+    __syncthreads();
+    const int64_t q1 = (u + 1) * per < live ? (u + 1) * per : live;
+    if (level == 0) {
+      for (int64_t q = u * per; q < q1; ++q) {
+        const int64_t r0 = q * mc;
+        const int m = (int)((rows - r0) < mc ? (rows - r0) : mc);
+        for (int c = warp; c < n; c += nwarps) {
+          E* dst = X + (int64_t)c * ldx;
+          if (b.ptr32) {
+            const float* src = b.ptr32 + (int64_t)c * b.ld + r0;
+#pragma unroll 4
+            for (int i = lane; i < m; i += 32) dst[i] = (E)src[i];
+          } else {
+            const double* src = b.ptr + (int64_t)c * b.ld + r0;
+#pragma unroll 4
+            for (int i = lane; i < m; i += 32) dst[i] = (E)src[i];
+          }
+        }
+        __syncthreads();
+        fold_chunk<E>(X, ldx, m, 1, n, 0, false, T, red);
+      }
+    } else if (stack >= 2) {
+      for (int64_t q = u * per; q < q1; q += stack) {
+        const int cnt = (int)((q1 - q) < stack ? (q1 - q) : stack);
+        for (int c = warp; c < n; c += nwarps) {
+          E* dst = X + (int64_t)c * ldx;
+          for (int idx = lane; idx < cnt * n; idx += 32) {
+            const int t = idx / n, r = idx - t * n;
+            dst[idx] = (E)tri_in[(q + t) * n * n + (int64_t)c * n + r];
+          }
+        }
+        __syncthreads();
+        fold_chunk<E>(X, ldx, n, cnt, n, 0, true, T, red);
+      }
+    } else {
+      for (int64_t q = u * per; q < q1; ++q) {
+        const double* src = tri_in + q * n * n;
+        for (int r0 = 0; r0 < n; r0 += mc) {
+          const int m = (n - r0) < mc ? (n - r0) : mc;
+          for (int c = warp; c < n; c += nwarps) {
+            E* dst = X + (int64_t)c * ldx;
+            for (int i = lane; i < m; i += 32) dst[i] = (E)src[(int64_t)c * n + r0 + i];
+          }
+          __syncthreads();
+          fold_chunk<E>(X, ldx, m, 1, n, r0, true, T, red);
+        }
+      }
+    }
+    double* tri = tri_out + u * n * n;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      const int c = idx / n, r = idx - c * n;
+      tri[idx] = r <= c ? (double)T[(int64_t)r * n + c] : 0.0;
+    }
+    __syncthreads();
+  }
+}
+
+static size_t fold_budget(bool mixed) { return mixed ? kFoldSmemF32 : kSmemCap; }
+
+static size_t fold_smem(const TsqrBlock& b, size_t esz) {
+  size_t e = (size_t)fold_red_elems(b.n) + (size_t)(b.tile + 1) * b.n;
+  if (b.fold_tsmem) e += (size_t)b.n * b.n;
+  return e * esz;
+}
+
+static int64_t fold_resident(bool mixed) { return mixed ? 152 * 2 : 152; }
+
+// units (triangles written) at a level, from the allocation bound of the rows
+static int64_t fold_units(const TsqrBlock& b, int level) {
+  int64_t u = (b.bound + b.tile - 1) / b.tile;
+  u = (u + b.seg - 1) / b.seg;                // at most fold_g0 on the device: seg grows with rows
+  for (int l = 1; l <= level; ++l) u = (u + b.fan - 1) / b.fan;
+  return u < 1 ? 1 : u;
+}
+
+template <typename E>
+static void launch_fold(const TsqrBlock& b, const double* tri_in, double* tri_out, int level, bool mixed,
+                        cudaStream_t st) {
+  int64_t grid = fold_units(b, level);
+  const int64_t cap = fold_resident(mixed);
+  if (grid > cap) grid = cap;
+  k_tsqr_fold<E><<<(unsigned)grid, kFoldThreads, fold_smem(b, sizeof(E)), st>>>(b, tri_in, tri_out, level);
+}
+
 // ------------------------------------------------------------------ final stack and R
 // One thread block places every block's triangle at its global columns: stack rows
 // [off_b, off_b + n_b), column-major with leading dimension stack_rows.
@@ -301,6 +628,45 @@ static int reg_tile_of(int N) {
 
 static size_t cta_smem(int lda, int n, size_t esz) { return (kRedElems + (size_t)lda * n) * esz; }
 
+// Fold path for a wide block: the chunk height that fills the shared-memory budget (the
+// triangle in shared memory when it takes at most a quarter of it, else in a global slot
+// per thread block), one leaf triangle per resident thread block (at most 16 chunks each on
+// the float path, whose error grows with the number of folds into one triangle).
+static bool fold_plan(TsqrBlock& b, bool mixed, size_t esz) {
+  const int n = b.n;
+  const size_t budget = fold_budget(mixed);
+  const size_t red = (size_t)fold_red_elems(n) * esz;
+  if (red >= budget) return false;
+  const bool tsm = (size_t)n * n * esz <= budget / 4;
+  const size_t rest = budget - red - (tsm ? (size_t)n * n * esz : 0);
+  int64_t mc = (int64_t)(rest / (esz * (size_t)n)) - 1;
+  mc = (mc / 32) * 32;
+  if (mc > 512) mc = 512;
+  if (mc < 32) return false;
+  b.fold = true;
+  b.fold_tsmem = tsm;
+  b.warp_min = 0;
+  b.tile = (int)mc;
+  // tree levels: as many triangles as one chunk stacks (at least 4, at most 16)
+  const int64_t stack = mc / n;
+  b.fan = (int)(stack < 4 ? 4 : (stack > 16 ? 16 : stack));
+  const int64_t chunks = (b.bound + mc - 1) / mc;
+  const int64_t res = fold_resident(mixed);
+  int64_t seg = (chunks + res - 1) / res;
+  if (mixed && seg > 16) seg = 16;
+  b.seg = seg < 1 ? 1 : seg;
+  int64_t u = (chunks + b.seg - 1) / b.seg;
+  b.fold_g0 = u < res ? u : res;
+  int levels = 0;
+  while (u > 1) {
+    u = (u + b.fan - 1) / b.fan;
+    ++levels;
+  }
+  b.levels = levels;
+  b.top = levels & 1;
+  return true;
+}
+
 void tsqr_plan_block(TsqrBlock& b, bool mixed, bool givens) {
   const int n = b.n;
   const size_t esz = mixed ? sizeof(float) : sizeof(double);
@@ -316,6 +682,8 @@ void tsqr_plan_block(TsqrBlock& b, bool mixed, bool givens) {
     // their trees with the block-per-tile kernel only, six triangles at a time
     b.fan = b.nreg <= 16 ? b.tile / n : 6;
     if (b.givens) b.tile = kGivensRows;       // leaf chunks of the Givens leaf
+  } else if (fold_plan(b, mixed, esz)) {
+    return;
   } else {
     b.warp_min = 0;
     int64_t t = (int64_t)(64 * 1024 / (esz * n));
@@ -340,6 +708,7 @@ void tsqr_plan_block(TsqrBlock& b, bool mixed, bool givens) {
 }
 
 int64_t tsqr_tri_elems(const TsqrBlock& b) {
+  if (b.fold) return fold_units(b, 0) * b.n * b.n;
   int64_t tiles = (b.bound + b.tile - 1) / b.tile;
   if (tiles < 1) tiles = 1;
   return tiles * b.n * b.n;
@@ -347,6 +716,7 @@ int64_t tsqr_tri_elems(const TsqrBlock& b) {
 
 int64_t tsqr_scratch_elems(const TsqrBlock& b, bool mixed) {
   if (b.nreg) return 0;
+  if (b.fold) return b.fold_tsmem ? 0 : fold_resident(mixed) * b.n * b.n;   // T slots (as doubles: room for floats)
   const size_t esz = mixed ? sizeof(float) : sizeof(double);
   int64_t need = 0;
   const int64_t grid = 152 * 2;
@@ -378,6 +748,10 @@ cudaError_t tsqr_set_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_tsqr_cta<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_tsqr_cta<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tsqr_fold<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tsqr_fold<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
   return e;
 }
 
@@ -393,7 +767,10 @@ void tsqr_leaf(const TsqrBlock& b, bool mixed, cudaStream_t st, int64_t* launche
     ++*launches;
     return;
   }
-  if (b.nreg) {
+  if (b.fold) {
+    if (mixed) launch_fold<float>(b, nullptr, b.tri[0], 0, true, st);
+    else launch_fold<double>(b, nullptr, b.tri[0], 0, false, st);
+  } else if (b.nreg) {
     if (mixed) {
       launch_reg_n<float>(b, nullptr, b.tri[0], 0, tiles, st);
       launch_cta<float>(b, nullptr, b.tri[0], 0, tiles, scratch, st, 1);
@@ -419,7 +796,11 @@ void tsqr_reduce(TsqrBlock& b, bool mixed, cudaStream_t st, int64_t* launches) {
   int cur = 0;
   for (int l = 0; l < b.levels; ++l) {
     const int64_t out_tiles = (tiles + b.fan - 1) / b.fan;
-    if (b.nreg && b.nreg <= 16) {
+    if (b.fold) {
+      if (mixed) launch_fold<float>(b, b.tri[cur], b.tri[cur ^ 1], l + 1, true, st);
+      else launch_fold<double>(b, b.tri[cur], b.tri[cur ^ 1], l + 1, false, st);
+      ++*launches;
+    } else if (b.nreg && b.nreg <= 16) {
       if (mixed) {
         launch_reg_n<float>(b, b.tri[cur], b.tri[cur ^ 1], div, out_tiles, st);
         launch_cta<float>(b, b.tri[cur], b.tri[cur ^ 1], div, out_tiles, scratch, st, 1);
