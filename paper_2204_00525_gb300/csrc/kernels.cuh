@@ -217,6 +217,7 @@ struct TsqrBlock {
   bool fold_tsmem;           // fold path: the running triangle lives in shared memory
   int64_t seg;               // fold path: at most this many chunks folded into one leaf triangle
   int64_t fold_g0;           // fold path: thread blocks of the leaf launch
+  bool fold_tc;              // fold path, float leaf: panels with tensor-core trailing updates
 };
 
 void tsqr_plan_block(TsqrBlock& b, bool mixed, bool givens = false);

@@ -71,7 +71,6 @@ __device__ void hh_qr(E* A, int lda, int m, int n, E* red) {
 }
 
 // ------------------------------------------------------------------ narrow tiles (n <= 32)
-constexpr int kSmallRed = 8 * 32 + 32 + 8;   // per-warp partial dot products, w, scalars
 
 // Householder QR of an m x n tile (n <= 32, column-major in shared memory) by 8 warps,
 // shaped for latency: per step one pass of dot products d_j = sum_{i>k} a_ik a_ij
@@ -273,10 +272,14 @@ constexpr int kFoldWorkers = 256;
 constexpr int kFoldPivotWarp = kFoldWorkers / 32;
 constexpr int kFoldMaxSlices = 8;
 constexpr size_t kFoldSmemF32 = 100 * 1024;   // two float blocks per SM (latency-bound)
+constexpr int kTcNb = 16;                      // tensor-core fold: panel width
+constexpr int kTcRec = kTcNb;                  // offset of 1/v0 behind tau' in the panel record
 
+// Shared scratch of a fold block, in elements: partial dots [max(256, n)], the step's T row
+// [n], scalars [4], and two staging rows [2 n] for T rows read from global memory.
 __host__ __device__ __forceinline__ int fold_red_elems(int n) {
   const int part = n > kFoldWorkers ? n : kFoldWorkers;
-  return ((part + n + 4) + 3) & ~3;
+  return ((part + 3 * n + 4) + 3) & ~3;
 }
 
 // Scalars of the fold's reflector in normalised form: v' = v / v0 = (1, x / v0) and
@@ -340,16 +343,164 @@ __device__ __forceinline__ int fold_slices(int cols) {
   return S < 1 ? 1 : S;
 }
 
+// One column step of a fold: reflector k, applied to the columns k+1 .. kend-1.  ra rows of
+// each of the P row blocks of X can be non-zero in column k, rb in column k+1 (rb >= ra; the
+// rows between hold zeros in column k).  T's row k is read from `rowk` (T itself, or the
+// staging row that the previous step filled when T is in global memory, tglob); the step
+// fills the staging row k+1 the same way, with its loads in flight through both passes.
+// rec (may be null) receives tau' and 1/v0 of the reflector.  Both passes end in a barrier.
+template <typename E>
+__device__ __forceinline__ void fold_step(E* X, int ldx, int h, int P, int n, int k, int kend, int ra, int rb, E* T,
+                                          bool tglob, E* red, E* rec) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  E* part = red;                                          // [S * cp] partial dots
+  E* trow = red + (n > kFoldWorkers ? n : kFoldWorkers);  // T[k][k+1..kend-1] of the step
+  E* sc = trow + n;                                       // tau', 1/v0, sigma of column k
+  E* tbuf = sc + 4;                                       // staging rows, [2][n]
+  const int cp = kend - 1 - k;                            // columns k+1 .. kend-1
+  const int S = fold_slices(cp);
+  const E* xk = X + (int64_t)k * ldx;
+  E* trk = T + (int64_t)k * n;
+  const E* rowk = tglob ? tbuf + (k & 1) * n : trk;
+  E tn = E(0);
+  const bool pre = tglob && tid < n - k - 1;              // staging of T[k+1][k+1..n-1]
+  if (pre) tn = __ldcg(T + (int64_t)(k + 1) * n + k + 1 + tid);
+  if (tid < kFoldWorkers) {
+    const int items = S * cp;
+    for (int e = tid; e < items; e += kFoldWorkers) {
+      const int jc = e % cp, s = e / cp;
+      const E* xj = xk + (int64_t)(jc + 1) * ldx;
+      E d0 = E(0), d1 = E(0), d2 = E(0), d3 = E(0);
+      for (int p = 0; p < P; ++p) {
+        const E* a = xk + p * h;
+        const E* c = xj + p * h;
+        int i = s;
+        for (; i + 3 * S < ra; i += 4 * S) {   // four rows in flight
+          const E a0 = a[i], a1 = a[i + S], a2 = a[i + 2 * S], a3 = a[i + 3 * S];
+          const E c0 = c[i], c1 = c[i + S], c2 = c[i + 2 * S], c3 = c[i + 3 * S];
+          d0 = fma(a0, c0, d0);
+          d1 = fma(a1, c1, d1);
+          d2 = fma(a2, c2, d2);
+          d3 = fma(a3, c3, d3);
+        }
+        for (; i < ra; i += S) d0 = fma(a[i], c[i], d0);
+      }
+      part[e] = (d0 + d1) + (d2 + d3);
+      if (s == 0) trow[jc] = rowk[k + 1 + jc];
+    }
+  } else if (tid == kFoldWorkers) {
+    const E sigma = sc[2], alpha = rowk[k];
+    E beta = alpha, taup = E(0), rv = E(0);             // a zero column: nothing to reflect
+    if (!f64_is_zero(sigma)) FoldScalars<E>::get(alpha, sigma, beta, taup, rv);
+    trk[k] = beta;
+    sc[0] = taup;
+    sc[1] = rv;
+    if (rec) {
+      rec[0] = taup;
+      rec[kTcRec] = rv;
+    }
+  }
+  __syncthreads();
+  const E taup = sc[0], rv = sc[1];
+  if (tid < kFoldWorkers) {
+    const int cq = cp - 1;                                // columns k+2 .. kend-1
+    const int S2 = fold_slices(cq);
+    const int items = S2 * cq;
+    for (int e = tid; e < items; e += kFoldWorkers) {
+      const int jc = e % cq + 1, s = e / cq;
+      E d = part[jc];
+      for (int q = 1; q < S; ++q) d += part[q * cp + jc];
+      const E tj = trow[jc];
+      const E wt = taup * fma(rv, d, tj);               // w' = tau' (T_kj + d_j / v0)
+      if (s == 0) trk[k + 1 + jc] = tj - wt;
+      const E w = wt * rv;                                // X[:, j] -= w' (X[:, k] / v0)
+      E* xj = X + (int64_t)(k + 1 + jc) * ldx;
+      for (int p = 0; p < P; ++p) {
+        const E* a = xk + p * h;
+        E* c = xj + p * h;
+        int i = s;
+        for (; i + 3 * S2 < ra; i += 4 * S2) {  // loads of four rows before their stores
+          const E a0 = a[i], a1 = a[i + S2], a2 = a[i + 2 * S2], a3 = a[i + 3 * S2];
+          const E c0 = c[i], c1 = c[i + S2], c2 = c[i + 2 * S2], c3 = c[i + 3 * S2];
+          c[i] = fma(-w, a0, c0);
+          c[i + S2] = fma(-w, a1, c1);
+          c[i + 2 * S2] = fma(-w, a2, c2);
+          c[i + 3 * S2] = fma(-w, a3, c3);
+        }
+        for (; i < ra; i += S2) c[i] = fma(-w, a[i], c[i]);
+      }
+    }
+  } else if (cp > 0) {
+    // warp 8: column k+1 and the sum of squares of its rows for the next step
+    E d = part[0];
+    for (int q = 1; q < S; ++q) d += part[q * cp];
+    const E tj = trow[0];
+    const E wt = taup * fma(rv, d, tj);
+    const E w = wt * rv;
+    E* xj = X + (int64_t)(k + 1) * ldx;
+    E sq = E(0), sq2 = E(0);
+    for (int p = 0; p < P; ++p) {
+      const E* a = xk + p * h;
+      E* c = xj + p * h;
+      int i = lane;
+      for (; i + 96 < rb; i += 128) {
+        const E a0 = a[i], a1 = a[i + 32], a2 = a[i + 64], a3 = a[i + 96];
+        const E c0 = c[i], c1 = c[i + 32], c2 = c[i + 64], c3 = c[i + 96];
+        const E v0 = fma(-w, a0, c0), v1 = fma(-w, a1, c1), v2 = fma(-w, a2, c2), v3 = fma(-w, a3, c3);
+        c[i] = v0;
+        c[i + 32] = v1;
+        c[i + 64] = v2;
+        c[i + 96] = v3;
+        sq = fma(v0, v0, sq);
+        sq2 = fma(v1, v1, sq2);
+        sq = fma(v2, v2, sq);
+        sq2 = fma(v3, v3, sq2);
+      }
+      for (; i < rb; i += 32) {
+        const E v = fma(-w, a[i], c[i]);
+        c[i] = v;
+        sq = fma(v, v, sq);
+      }
+    }
+    sq = fold_warp_sum(sq + sq2);
+    if (lane == 0) {
+      trk[k + 1] = tj - wt;
+      sc[2] = sq;
+    }
+  }
+  if (pre) tbuf[((k + 1) & 1) * n + k + 1 + tid] = tn;
+  __syncthreads();
+}
+
+// Sum of squares of column k of X over ra rows of its P row blocks into sc[2], and (T in
+// global memory) T's row k into its staging row; ends in a barrier.
+template <typename E>
+__device__ __forceinline__ void fold_column_start(const E* X, int ldx, int h, int P, int n, int k, int ra,
+                                                  const E* T, bool tglob, E* red) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  E* sc = red + (n > kFoldWorkers ? n : kFoldWorkers) + n;
+  E* tbuf = sc + 4;
+  if (tglob && tid < n - k) tbuf[(k & 1) * n + k + tid] = __ldcg(T + (int64_t)k * n + k + tid);
+  if (warp == kFoldPivotWarp) {
+    const E* x0 = X + (int64_t)k * ldx;
+    E sq = E(0);
+    for (int p = 0; p < P; ++p)
+      for (int i = lane; i < ra; i += 32) {
+        const E v = x0[p * h + i];
+        sq = fma(v, v, sq);
+      }
+    sq = fold_warp_sum(sq);
+    if (lane == 0) sc[2] = sq;
+  }
+  __syncthreads();
+}
+
 // Folds X into T.  X holds P row blocks of h rows each (row block p at rows [p h, p h + h),
 // leading dimension ldx).  Dense: every row may be non-zero.  tri: every row block holds
 // rows [r0, r0 + h) of an upper triangle, so that in column k only its first
 // k + 1 - r0 rows can be non-zero.
 template <typename E>
-__device__ void fold_chunk(E* X, int ldx, int h, int P, int n, int r0, bool tri, E* T, E* red) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  E* part = red;                                          // [S * cp] partial dots
-  E* trow = red + (n > kFoldWorkers ? n : kFoldWorkers);  // T[k][k+1..n-1] of the step
-  E* sc = trow + n;                                       // tau', 1/v0, next sigma, next alpha
+__device__ void fold_chunk(E* X, int ldx, int h, int P, int n, int r0, bool tri, E* T, bool tglob, E* red) {
   auto rows_at = [&](int k) -> int {
     if (!tri) return h;
     const int r = k + 1 - r0;
@@ -359,116 +510,245 @@ __device__ void fold_chunk(E* X, int ldx, int h, int P, int n, int r0, bool tri,
   // are the identity
   const int kbeg = tri ? (r0 < n ? r0 : n) : 0;
   if (kbeg >= n) return;
-  if (warp == kFoldPivotWarp) {
-    const int ra = rows_at(kbeg);
-    const E* x0 = X + (int64_t)kbeg * ldx;
-    E sq = E(0);
-    for (int p = 0; p < P; ++p)
-      for (int i = lane; i < ra; i += 32) {
-        const E v = x0[p * h + i];
-        sq = fma(v, v, sq);
-      }
-    sq = fold_warp_sum(sq);
-    if (lane == 0) {
-      sc[2] = sq;
-      sc[3] = T[(int64_t)kbeg * n + kbeg];
-    }
-  }
-  __syncthreads();
-  for (int k = kbeg; k < n; ++k) {
-    const int ra = rows_at(k), rb = rows_at(k + 1);   // rows [ra, rb) have X[i][k] = 0
-    const int cp = n - 1 - k;                         // columns k+1 .. n-1
-    const int S = fold_slices(cp);
-    const E* xk = X + (int64_t)k * ldx;
-    E* trk = T + (int64_t)k * n;
-    if (tid < kFoldWorkers) {
-      const int items = S * cp;
-      for (int e = tid; e < items; e += kFoldWorkers) {
-        const int jc = e % cp, s = e / cp;
-        if (s == 0) trow[jc] = trk[k + 1 + jc];
-        const E* xj = xk + (int64_t)(jc + 1) * ldx;
-        E d0 = E(0), d1 = E(0);
-        for (int p = 0; p < P; ++p) {
-          const E* a = xk + p * h;
-          const E* c = xj + p * h;
-          int i = s;
-          for (; i + S < ra; i += 2 * S) {
-            d0 = fma(a[i], c[i], d0);
-            d1 = fma(a[i + S], c[i + S], d1);
+  fold_column_start<E>(X, ldx, h, P, n, kbeg, rows_at(kbeg), T, tglob, red);
+  for (int k = kbeg; k < n; ++k)
+    fold_step<E>(X, ldx, h, P, n, k, n, rows_at(k), rows_at(k + 1), T, tglob, red, nullptr);
+}
+
+// ------------------------------------------------------------------ tensor-core fold (float leaf)
+// The float leaf folds a chunk by panels of kTcNb columns.  The panel's reflectors come from
+// the column steps above, restricted to the panel; the trailing columns then take all of
+// them at once in compact WY form: Q = H_0 ... H_{b-1} = I - Y Tw Y^T with
+// y_q = (e_{p0+q} on T's rows, x_q / v0_q on X's rows), Tw upper triangular (Tw_qq = tau'_q,
+// Tw[0:q, q] = -tau'_q Tw[0:q, 0:q] z, z_r = y_r^T y_q = (x_r^T x_q) / (v0_r v0_q)), so that
+//   P  = X_v^T [X_panel X_trail]                 (tensor cores; its panel part gives x_r^T x_q)
+//   W  = T[p0.., trail] + diag(1/v0) P_trail,  W' = Tw^T W,
+//   T[p0.., trail] -= W',  X_trail -= X_v diag(1/v0) W'   (tensor cores).
+// The tensor-core products are tf32 with every operand split into three tf32 parts
+// (a = a0 + a1 + a2 exactly to 2^-33 |a|) and the six products of order <= 2 kept, which is
+// better than float; every k-step of 8 starts from a zero accumulator and is added to the
+// running sums in float on the CUDA cores, so the accumulation rounds like a float dot.
+constexpr int kTcLdw = 20;      // leading dimension of the column-by-panel staging buffer
+
+__host__ __device__ __forceinline__ int fold_tc_extra(int n) {
+  return ((n * kTcLdw + kTcNb * kTcNb + 2 * kTcNb) + 3) & ~3;
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// x = p0 + p1 + p2, all tf32 (each remainder is exact in float)
+__device__ __forceinline__ void split3_tf32(float x, uint32_t& p0, uint32_t& p1, uint32_t& p2) {
+  p0 = to_tf32(x);
+  const float r1 = x - __uint_as_float(p0);
+  p1 = to_tf32(r1);
+  p2 = to_tf32(r1 - __uint_as_float(p1));
+}
+
+// d += a b, one m16n8k8 tf32 product with float accumulation
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// d = a b (16 x 8 x 8) from a zero accumulator: the six split products, smallest first
+__device__ __forceinline__ void mma_6xtf32(float (&d)[4], const float (&a)[4], const float (&b)[2]) {
+  uint32_t a0[4], a1[4], a2[4], b0[2], b1[2], b2[2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) split3_tf32(a[i], a0[i], a1[i], a2[i]);
+#pragma unroll
+  for (int i = 0; i < 2; ++i) split3_tf32(b[i], b0[i], b1[i], b2[i]);
+  d[0] = d[1] = d[2] = d[3] = 0.f;
+  mma_tf32(d, a2, b0);
+  mma_tf32(d, a1, b1);
+  mma_tf32(d, a0, b2);
+  mma_tf32(d, a1, b0);
+  mma_tf32(d, a0, b1);
+  mma_tf32(d, a0, b0);
+}
+
+// Folds the dense chunk X (m rows, leading dimension ldx = 4 mod 32, against bank
+// conflicts of the fragment loads) into T.  ext: kTcLdw x n staging, Tw, tau', 1/v0.
+// Fragment layouts of mma.m16n8k8 (g = lane / 4, t = lane % 4): A (16 x 8) a0 = (g, t),
+// a1 = (g + 8, t), a2 = (g, t + 4), a3 = (g + 8, t + 4); B (8 x 8) b0 = (t, g),
+// b1 = (t + 4, g); C (16 x 8) c0 = (g, 2t), c1 = (g, 2t + 1), c2 = (g + 8, 2t),
+// c3 = (g + 8, 2t + 1).
+__device__ void fold_chunk_tc(float* X, int ldx, int m, int n, float* T, bool tglob, float* red, float* ext) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, t4 = lane & 3;
+  float* Ps = ext;                         // [n][kTcLdw]: P (column j - p0), then diag(1/v0) W'
+  float* Tw = ext + n * kTcLdw;            // Tw[r * kTcNb + q]
+  float* tpv = Tw + kTcNb * kTcNb;         // tau' of the panel's reflectors
+  float* rvv = tpv + kTcRec;               // 1/v0 of the panel's reflectors
+  fold_column_start<float>(X, ldx, m, 1, n, 0, m, T, tglob, red);
+  for (int p0 = 0; p0 < n; p0 += kTcNb) {
+    const int b = (n - p0) < kTcNb ? (n - p0) : kTcNb;
+    const int kend = p0 + b;
+    for (int k = p0; k < kend; ++k) fold_step<float>(X, ldx, m, 1, n, k, kend, m, m, T, tglob, red, tpv + (k - p0));
+    const int c = n - kend;                  // trailing columns
+    if (c <= 0) break;
+    const float* Xv = X + (int64_t)p0 * ldx; // x_q = column p0 + q
+    // ---- P = X_v^T [X_panel X_trail]: 16 x (n - p0), K = m
+    {
+      const int ncol = n - p0;
+      const int NT = (ncol + 7) >> 3, KT = (m + 7) >> 3;
+      if (warp < kFoldPivotWarp) {
+        for (int nt = warp; nt < NT; nt += kFoldPivotWarp) {
+          float sum[4] = {0.f, 0.f, 0.f, 0.f};
+          const int jb = nt * 8 + g;
+          const bool jok = jb < ncol;
+          const float* xb = Xv + (int64_t)jb * ldx;
+          const float* xa0 = Xv + (int64_t)g * ldx;
+          const float* xa1 = Xv + (int64_t)(g + 8) * ldx;
+          const bool q0ok = g < b, q1ok = g + 8 < b;
+          for (int kt = 0; kt < KT; kt += 2) {   // two independent k-steps in flight
+            float d[2][4];
+#pragma unroll
+            for (int h2 = 0; h2 < 2; ++h2) {
+              const int i0 = (kt + h2) * 8 + t4, i1 = i0 + 4;
+              const bool r0ok = i0 < m, r1ok = i1 < m;
+              const float a[4] = {(q0ok && r0ok) ? xa0[i0] : 0.f, (q1ok && r0ok) ? xa1[i0] : 0.f,
+                                  (q0ok && r1ok) ? xa0[i1] : 0.f, (q1ok && r1ok) ? xa1[i1] : 0.f};
+              const float bb[2] = {(jok && r0ok) ? xb[i0] : 0.f, (jok && r1ok) ? xb[i1] : 0.f};
+              mma_6xtf32(d[h2], a, bb);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) sum[i] += d[0][i] + d[1][i];
           }
-          if (i < ra) d0 = fma(a[i], c[i], d0);
+          const int j0 = nt * 8 + 2 * t4;
+          if (j0 < ncol) {
+            Ps[j0 * kTcLdw + g] = sum[0];
+            Ps[j0 * kTcLdw + g + 8] = sum[2];
+          }
+          if (j0 + 1 < ncol) {
+            Ps[(j0 + 1) * kTcLdw + g] = sum[1];
+            Ps[(j0 + 1) * kTcLdw + g + 8] = sum[3];
+          }
         }
-        part[e] = d0 + d1;
       }
-    } else if (tid == kFoldWorkers) {
-      const E sigma = sc[2], alpha = sc[3];
-      E beta = alpha, taup = E(0), rv = E(0);           // a zero column: nothing to reflect
-      if (!f64_is_zero(sigma)) FoldScalars<E>::get(alpha, sigma, beta, taup, rv);
-      trk[k] = beta;
-      sc[0] = taup;
-      sc[1] = rv;
     }
     __syncthreads();
-    const E taup = sc[0], rv = sc[1];
-    if (tid < kFoldWorkers) {
-      const int cq = cp - 1;                          // columns k+2 .. n-1
-      const int S2 = fold_slices(cq);
-      const int items = S2 * cq;
-      for (int e = tid; e < items; e += kFoldWorkers) {
-        const int jc = e % cq + 1, s = e / cq;
-        E d = part[jc];
-        for (int q = 1; q < S; ++q) d += part[q * cp + jc];
-        const E tj = trow[jc];
-        const E wt = taup * fma(rv, d, tj);             // w' = tau' (T_kj + d_j / v0)
-        if (s == 0) trk[k + 1 + jc] = tj - wt;
-        const E w = wt * rv;                              // X[:, j] -= w' (X[:, k] / v0)
-        E* xj = X + (int64_t)(k + 1 + jc) * ldx;
-        for (int p = 0; p < P; ++p) {
-          const E* a = xk + p * h;
-          E* c = xj + p * h;
-          for (int i = s; i < ra; i += S2) c[i] = fma(-w, a[i], c[i]);
+    // ---- Tw, column by column (one warp; Ps[q][s] = x_s^T x_q for s < q)
+    if (warp == 0) {
+      for (int q = 0; q < b; ++q) {
+        const float tq = tpv[q], rq = rvv[q];
+        float val = 0.f;
+        if (lane < q) {
+          float acc = 0.f;
+          for (int s2 = lane; s2 < q; ++s2) acc = fmaf(Tw[lane * kTcNb + s2], Ps[q * kTcLdw + s2] * rvv[s2] * rq, acc);
+          val = -tq * acc;
+        } else if (lane == q) {
+          val = tq;
+        }
+        __syncwarp();
+        if (lane <= q) Tw[lane * kTcNb + q] = val;
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    // ---- W' = Tw^T (T[p0.., j] + diag(1/v0) P[:, j]) per trailing column; T rows updated
+    for (int jj = tid; jj < c; jj += blockDim.x) {
+      const int j = kend + jj, jr = b + jj;
+      float w[kTcNb];
+#pragma unroll
+      for (int q = 0; q < kTcNb; ++q)
+        w[q] = q < b ? fmaf(rvv[q], Ps[jr * kTcLdw + q], T[(int64_t)(p0 + q) * n + j]) : 0.f;
+#pragma unroll
+      for (int q = kTcNb - 1; q >= 0; --q) {   // in place from the last row: w[r], r <= q, still W
+        if (q < b) {
+          float acc = 0.f;
+#pragma unroll
+          for (int r = 0; r <= q; ++r) acc = fmaf(Tw[r * kTcNb + q], w[r], acc);
+          w[q] = acc;
         }
       }
-    } else if (cp > 0) {
-      // warp 8: column k+1 and the sum of squares of its rows for the next step
-      const E alpha_next = lane == 0 ? T[(int64_t)(k + 1) * n + k + 1] : E(0);
-      E d = part[0];
-      for (int q = 1; q < S; ++q) d += part[q * cp];
-      const E tj = trow[0];
-      const E wt = taup * fma(rv, d, tj);
-      const E w = wt * rv;
-      E* xj = X + (int64_t)(k + 1) * ldx;
-      E sq = E(0);
-      for (int p = 0; p < P; ++p) {
-        const E* a = xk + p * h;
-        E* c = xj + p * h;
-        for (int i = lane; i < rb; i += 32) {
-          const E v = fma(-w, a[i], c[i]);
-          c[i] = v;
-          sq = fma(v, v, sq);
+#pragma unroll
+      for (int q = 0; q < kTcNb; ++q) {
+        if (q < b) {
+          T[(int64_t)(p0 + q) * n + j] -= w[q];
+          Ps[jr * kTcLdw + q] = rvv[q] * w[q];
+        } else {
+          Ps[jr * kTcLdw + q] = 0.f;
         }
       }
+    }
+    __syncthreads();
+    // ---- X_trail -= X_v B, B = diag(1/v0) W' (K = 16)
+    {
+      const int MT = (m + 15) >> 4, NT = (c + 7) >> 3;
+      if (warp < kFoldPivotWarp) {
+        for (int u = warp; u < MT * NT; u += kFoldPivotWarp) {
+          const int mt = u % MT, nt = u / MT;
+          const int r0 = mt * 16 + g, r1 = r0 + 8;
+          const int jc0 = nt * 8 + 2 * t4, jb = nt * 8 + g;
+          const bool r0ok = r0 < m, r1ok = r1 < m, c0ok = jc0 < c, c1ok = jc0 + 1 < c, jok = jb < c;
+          float* x0 = X + (int64_t)(kend + jc0) * ldx;
+          float* x1 = x0 + ldx;
+          float prod[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int kt = 0; kt < 2; ++kt) {
+            const int q0 = kt * 8 + t4, q1 = q0 + 4;
+            const float* v0p = Xv + (int64_t)q0 * ldx;
+            const float* v1p = Xv + (int64_t)q1 * ldx;
+            const bool q0ok = q0 < b, q1ok = q1 < b;
+            const float a[4] = {(r0ok && q0ok) ? v0p[r0] : 0.f, (r1ok && q0ok) ? v0p[r1] : 0.f,
+                                (r0ok && q1ok) ? v1p[r0] : 0.f, (r1ok && q1ok) ? v1p[r1] : 0.f};
+            const float bb[2] = {jok ? Ps[(b + jb) * kTcLdw + q0] : 0.f, jok ? Ps[(b + jb) * kTcLdw + q1] : 0.f};
+            float d[4];
+            mma_6xtf32(d, a, bb);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) prod[i] += d[i];
+          }
+          if (c0ok && r0ok) x0[r0] -= prod[0];
+          if (c1ok && r0ok) x1[r0] -= prod[1];
+          if (c0ok && r1ok) x0[r1] -= prod[2];
+          if (c1ok && r1ok) x1[r1] -= prod[3];
+        }
+      }
+    }
+    __syncthreads();
+    // ---- the next panel's first column: its sum of squares (its T row is staged already)
+    if (warp == kFoldPivotWarp) {
+      const float* xn = X + (int64_t)kend * ldx;
+      float sq = 0.f;
+      for (int i = lane; i < m; i += 32) sq = fmaf(xn[i], xn[i], sq);
       sq = fold_warp_sum(sq);
-      if (lane == 0) {
-        trk[k + 1] = tj - wt;
-        sc[2] = sq;
-        sc[3] = alpha_next;
-      }
+      if (lane == 0) red[(n > kFoldWorkers ? n : kFoldWorkers) + n + 2] = sq;
     }
     __syncthreads();
   }
 }
 
+template <typename E>
+struct FoldLeafTc {
+  __device__ static bool run(E*, int, int, int, E*, bool, E*, E*) { return false; }
+};
+template <>
+struct FoldLeafTc<float> {
+  __device__ static bool run(float* X, int ldx, int m, int n, float* T, bool tglob, float* red, float* ext) {
+    fold_chunk_tc(X, ldx, m, n, T, tglob, red, ext);
+    return true;
+  }
+};
+
 // level 0: the leaf over the block's rows; level l > 0: tree level l over tri_in.
 template <typename E>
-__global__ void __launch_bounds__(kFoldThreads) k_tsqr_fold(TsqrBlock b, const double* tri_in, double* tri_out,
-                                                            int level) {
+__global__ void __launch_bounds__(kFoldThreads, sizeof(E) == 4 ? 2 : 1)
+    k_tsqr_fold(TsqrBlock b, const double* tri_in, double* tri_out, int level) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n = b.n, mc = b.tile, ldx = mc + 1;
+  const int n = b.n, mc = b.tile;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const bool tc = b.fold_tc && level == 0;    // tensor-core panels (float leaf)
+  const int ldx_alloc = mc + (b.fold_tc ? 4 : 1);
   E* red = reinterpret_cast<E*>(smem_raw);
-  E* X = red + fold_red_elems(n);
-  E* T = b.fold_tsmem ? X + (int64_t)ldx * n : static_cast<E*>(b.scratch) + (int64_t)blockIdx.x * n * n;
+  E* ext = red + fold_red_elems(n);
+  E* X = ext + (b.fold_tc ? fold_tc_extra(n) : 0);
+  E* T = b.fold_tsmem ? X + (int64_t)ldx_alloc * n : static_cast<E*>(b.scratch) + (int64_t)blockIdx.x * n * n;
+  const bool tglob = !b.fold_tsmem;
   const int64_t rows = block_rows(b);
   // chunks per leaf triangle from the live rows: the leaf's thread blocks share them evenly
   const int64_t chunks = (rows + mc - 1) / mc;
@@ -487,6 +767,7 @@ __global__ void __launch_bounds__(kFoldThreads) k_tsqr_fold(TsqrBlock b, const d
       return;
     }
   }
+  const int ldx = tc ? mc + 4 : mc + 1;      // odd for the column steps, 4 mod 32 for the fragments
   const int stack = mc / n;                   // whole triangles per chunk on tree levels
   int64_t units = (live + per - 1) / per;
   if (units < 1) units = 1;                   // an empty block still leaves a (zero) triangle
@@ -511,7 +792,8 @@ __global__ void __launch_bounds__(kFoldThreads) k_tsqr_fold(TsqrBlock b, const d
           }
         }
         __syncthreads();
-        fold_chunk<E>(X, ldx, m, 1, n, 0, false, T, red);
+        if (!(tc && FoldLeafTc<E>::run(X, ldx, m, n, T, tglob, red, ext)))
+          fold_chunk<E>(X, ldx, m, 1, n, 0, false, T, tglob, red);
       }
     } else if (stack >= 2) {
       for (int64_t q = u * per; q < q1; q += stack) {
@@ -524,7 +806,7 @@ __global__ void __launch_bounds__(kFoldThreads) k_tsqr_fold(TsqrBlock b, const d
           }
         }
         __syncthreads();
-        fold_chunk<E>(X, ldx, n, cnt, n, 0, true, T, red);
+        fold_chunk<E>(X, ldx, n, cnt, n, 0, true, T, tglob, red);
       }
     } else {
       for (int64_t q = u * per; q < q1; ++q) {
@@ -536,7 +818,7 @@ __global__ void __launch_bounds__(kFoldThreads) k_tsqr_fold(TsqrBlock b, const d
             for (int i = lane; i < m; i += 32) dst[i] = (E)src[(int64_t)c * n + r0 + i];
           }
           __syncthreads();
-          fold_chunk<E>(X, ldx, m, 1, n, r0, true, T, red);
+          fold_chunk<E>(X, ldx, m, 1, n, r0, true, T, tglob, red);
         }
       }
     }
@@ -552,7 +834,8 @@ __global__ void __launch_bounds__(kFoldThreads) k_tsqr_fold(TsqrBlock b, const d
 static size_t fold_budget(bool mixed) { return mixed ? kFoldSmemF32 : kSmemCap; }
 
 static size_t fold_smem(const TsqrBlock& b, size_t esz) {
-  size_t e = (size_t)fold_red_elems(b.n) + (size_t)(b.tile + 1) * b.n;
+  size_t e = (size_t)fold_red_elems(b.n) + (size_t)(b.tile + (b.fold_tc ? 4 : 1)) * b.n;
+  if (b.fold_tc) e += (size_t)fold_tc_extra(b.n);
   if (b.fold_tsmem) e += (size_t)b.n * b.n;
   return e * esz;
 }
@@ -634,17 +917,20 @@ static size_t cta_smem(int lda, int n, size_t esz) { return (kRedElems + (size_t
 // the float path, whose error grows with the number of folds into one triangle).
 static bool fold_plan(TsqrBlock& b, bool mixed, size_t esz) {
   const int n = b.n;
+  if (n > kFoldWorkers) return false;          // T rows are staged one element per worker thread
   const size_t budget = fold_budget(mixed);
-  const size_t red = (size_t)fold_red_elems(n) * esz;
+  const bool tc = mixed;                      // float leaf: tensor-core panels
+  const size_t red = ((size_t)fold_red_elems(n) + (tc ? (size_t)fold_tc_extra(n) : 0)) * esz;
   if (red >= budget) return false;
   const bool tsm = (size_t)n * n * esz <= budget / 4;
   const size_t rest = budget - red - (tsm ? (size_t)n * n * esz : 0);
-  int64_t mc = (int64_t)(rest / (esz * (size_t)n)) - 1;
+  int64_t mc = (int64_t)(rest / (esz * (size_t)n)) - (tc ? 4 : 1);
   mc = (mc / 32) * 32;
   if (mc > 512) mc = 512;
   if (mc < 32) return false;
   b.fold = true;
   b.fold_tsmem = tsm;
+  b.fold_tc = tc;
   b.warp_min = 0;
   b.tile = (int)mc;
   // tree levels: as many triangles as one chunk stacks (at least 4, at most 16)
