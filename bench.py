@@ -180,7 +180,7 @@ def run_plan_only(args):
     import torch
     from paper_2204_00525_gb300 import binding
     binding.load(build_if_missing=True)
-    db = synth.path3(seed=2, rows=args.rows)
+    db = wide_workload(args.workload) if args.workload != "path3" else synth.path3(seed=2, rows=args.rows)
     dev_inputs = make_inputs(db, torch, "cuda")
     prec = binding.FIGARO_PREC_MIXED if args.plan_only.startswith("mixed") else binding.FIGARO_PREC_FP64
     p = binding.JoinPlan(dev_inputs, db.parent, precision=prec, stage_timing=args.plan_only.endswith("staged"),
@@ -189,6 +189,60 @@ def run_plan_only(args):
     ms = time_steps(p, torch, args.steps, args.warmup, lambda: None)
     p.close()
     log(f"{args.plan_only}: {ms:.3f} ms per step")
+
+
+def wide_workload(name):
+    """The wide-block workloads: the 5M-row many-to-many star (16 columns per relation,
+    a 48-column generalized-tail block of ~5M rows) and the 10M-row snowflake (50 columns per
+    relation, 10 of the 200 scaled by 1e4; 100-, 150- and 200-column blocks)."""
+    return synth.star() if name == "star" else synth.snowflake()
+
+
+def run_wide(args):
+    """--wide: R of the star and snowflake workloads (blocks wider than 32 columns, reduced
+    by the streamed fold), FP64 and mixed, one call at a time (CUDA events), with the
+    dominant block's leaf time from a stage-timed plan.  Prints one JSON line."""
+    import numpy as np
+    import torch
+    from paper_2204_00525_gb300 import binding
+    binding.load(build_if_missing=True)
+    out = []
+    for name in ("star", "snowflake"):
+        db = wide_workload(name)
+        dev_inputs = make_inputs(db, torch, "cuda")
+        cells = db.input_cells()
+        row = {"workload": db.description, "input_cells": cells}
+        Rs = {}
+        for tag, prec in (("fp64", binding.FIGARO_PREC_FP64), ("mixed", binding.FIGARO_PREC_MIXED)):
+            p = binding.JoinPlan(dev_inputs, db.parent, precision=prec, stream=torch.cuda.current_stream())
+            p._R = torch.empty(db.n_cols, db.n_cols, dtype=torch.float64, device="cuda")
+            ms = time_steps(p, torch, args.steps, args.warmup, lambda: None)
+            Rs[tag] = p.qr_r().cpu().numpy()
+            p.close()
+            ps = binding.JoinPlan(dev_inputs, db.parent, precision=prec, stage_timing=True,
+                                  stream=torch.cuda.current_stream())
+            ps.qr_r()
+            ps.reset_stage_times()
+            ps.qr_r()
+            blocks = ps.block_times()
+            ps.close()
+            leaf_ms, n_cols, rows = max(blocks)
+            flops = 2.0 * rows * n_cols * n_cols
+            row[tag] = {"ms_per_step": ms, "cells_per_s": cells / (ms * 1e-3),
+                        "dominant_block": {"n_cols": n_cols, "rows": rows, "leaf_ms": leaf_ms,
+                                           "leaf_tflops": flops / (leaf_ms * 1e-3) / 1e12}}
+        G = Rs["fp64"].T @ Rs["fp64"]
+        row["mixed"]["rel_err_RtR_vs_fp64"] = float(np.linalg.norm(Rs["mixed"].T @ Rs["mixed"] - G) /
+                                                    np.linalg.norm(G))
+        row["mixed"]["speedup_vs_fp64"] = row["fp64"]["ms_per_step"] / row["mixed"]["ms_per_step"]
+        out.append(row)
+        del dev_inputs
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "wide-block workloads: time to R, one call at a time", "unit": "ms",
+                      "higher_is_better": False, "steps": args.steps, "warmup": args.warmup,
+                      "data": "synthetic (seeded)", "fp64_peak_tflops_derived": FP64_PEAK_TFLOPS,
+                      "leaf_flops": "2 rows n^2 per block (Householder on the block's rows)",
+                      "workloads": out}), flush=True)
 
 
 def run_batch(args):
@@ -510,6 +564,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plan-only", choices=["fp64", "mixed", "fp64-staged", "mixed-staged"],
                     help="profiling aid: run one plan only and print no JSON line")
+    ap.add_argument("--workload", choices=["path3", "star", "snowflake"], default="path3",
+                    help="workload of --plan-only")
+    ap.add_argument("--wide", action="store_true",
+                    help="measure the wide-block workloads (star, snowflake) instead")
     ap.add_argument("--batch-instances", type=int, default=0,
                     help="measure the batched-instances workload (first K of 256) instead")
     args = ap.parse_args()
@@ -519,6 +577,8 @@ def main():
         run_plan_only(args)
     elif args.batch_instances:
         run_batch(args)
+    elif args.wide:
+        run_wide(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
