@@ -10,11 +10,14 @@
 // Householder (MKL) or per-thread Givens (THIN); the TSQR tree is the GPU form of the
 // same block-then-stack scheme.
 //
-// Two kernels do the QR of a tile:
-//   n <= 32: one warp per tile, the tile in registers (k_tsqr_reg), every loop bound a
-//            compile-time constant so that no predicated-off FP64 instruction is issued;
-//   n >  32: one thread block per tile in shared memory (k_tsqr_cta).
-// Both are persistent over the live tiles: the row counts are only known on the device.
+// The kernels:
+//   n <= 32:       one warp per tile, the tile in registers (k_tsqr_reg), every loop bound
+//                  a compile-time constant so that no predicated-off FP64 instruction is
+//                  issued; levels with few tiles take one thread block per tile (k_tsqr_cta);
+//   33 <= n <= 256: the streamed fold (k_tsqr_fold): one resident triangle per thread block,
+//                  row chunks folded into it, structured tree levels;
+//   n > 256:       one thread block per tile in shared memory or a global slot (k_tsqr_cta).
+// All are persistent over the live tiles: the row counts are only known on the device.
 //
 // Precision: FP64 throughout, or (mixed) FP32 leaf tiles and tree levels with the final QR
 // of the stacked block triangles in FP64.
