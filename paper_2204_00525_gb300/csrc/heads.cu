@@ -307,8 +307,10 @@ __global__ void __launch_bounds__(256) k_leaf_agg_mx(LeafParams p) {
   }
 }
 
+// Latency-bound: three blocks per SM on the mixed path (80 registers); the refinement's
+// variant (LO, the low floats kept too) holds more state and stays at two.
 template <bool LO>
-__global__ void __launch_bounds__(256, 2) k_leaf_emit_mx(LeafParams p) {
+__global__ void __launch_bounds__(256, LO ? 2 : 3) k_leaf_emit_mx(LeafParams p) {
   const int lane = threadIdx.x & 31;
   const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -316,14 +318,12 @@ __global__ void __launch_bounds__(256, 2) k_leaf_emit_mx(LeafParams p) {
     const int64_t e0 = t * kHtTile + (int64_t)lane * kHtItems;
     LeafRow rw[kHtItems];
     dfl gam[kHtItems];                    // sqrt(Phi_circ) beta_p (the low part only when refining)
-    dfl pos[kHtItems];
 #pragma unroll
     for (int i = 0; i < kHtItems; ++i) {
       rw[i] = leaf_row(p, e0 + i);
       const bool tail = rw[i].ok && rw[i].pos > 0;
       const double g = tail ? p.sq_phic[rw[i].g] * p.beta[rw[i].pos].x : 0.0;
       gam[i] = LO ? df_from_double(g) : dfl{(float)g, 0.0f};
-      pos[i] = df_from_count(rw[i].pos);
     }
     for (int c = 0; c < p.N; ++c) {
       const int64_t slot = (int64_t)c * p.n_tiles + t;
@@ -339,7 +339,9 @@ __global__ void __launch_bounds__(256, 2) k_leaf_emit_mx(LeafParams p) {
         const dfl x = df_from_double(xs[i]);
         if (rw[i].pos == 0) run = dfl{0.0f, 0.0f};
         if (rw[i].pos > 0) {
-          const dfl d = df_add(df_mul(x, pos[i]), df_neg(run));
+          // p as a float pair, formed again per column (a few FP32 operations) rather than
+          // held in registers for the whole tile
+          const dfl d = df_add(df_mul(x, df_from_count(rw[i].pos)), df_neg(run));
           const int64_t row = e0 + i - rw[i].g - 1;
           if (LO) {                        // the double-float tail, kept for the refinement's Gram
             const dfl tt = df_mul(d, gam[i]);
