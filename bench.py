@@ -12,6 +12,11 @@ roofline, and the CPU oracle on a bounded sample of the same workload.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl figaro|reference]
 Under torchrun every rank runs an independent instance (weak scaling; the path has no
 data exchange) and rank 0 prints one JSON line.
+
+Other workloads (one JSON line each, not the benchmark line): --batch-instances K (the
+batch of independent two-relation joins as one graph launch) and --wide (the star and
+snowflake joins, whose blocks of 33-256 columns go through the streamed fold).
+--plan-only runs one plan on a chosen workload without output, for ncu captures.
 """
 import os
 
