@@ -1,0 +1,54 @@
+"""bench.py's output contract, on the CPU: the reference arm (the oracle on a bounded
+sample) prints exactly one JSON line with the contract's keys; a rank other than 0 prints
+nothing and exits 0; the argument parser accepts every documented mode."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+BENCH = os.path.join(ROOT, "bench.py")
+
+
+def run(args, env_extra=None):
+    env = dict(os.environ)
+    env.update(env_extra or {})
+    return subprocess.run([sys.executable, BENCH] + args, capture_output=True, text=True, env=env,
+                          timeout=600, cwd=ROOT)
+
+
+def test_reference_arm_json_line():
+    r = run(["--impl", "reference", "--sample-rows", "3000", "--steps", "1", "--warmup", "1"])
+    assert r.returncode == 0, r.stderr
+    lines = [l for l in r.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["steps"] == 1 and d["warmup"] == 1 and d["n_gpus"] == 1
+    assert "workload" in d["config"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    e = d["e2e"]
+    assert e["value"] == d["value"] and e["unit"] == d["unit"]
+    assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+    sys.path.insert(0, ROOT)
+    import bench
+    assert d["metric"] == bench.METRIC
+
+
+def test_reference_arm_other_rank_is_silent():
+    r = run(["--impl", "reference", "--sample-rows", "3000", "--steps", "1", "--warmup", "1"],
+            {"RANK": "1", "WORLD_SIZE": "2"})
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == ""
+
+
+def test_documented_modes_parse():
+    r = run(["--help"])
+    assert r.returncode == 0
+    for flag in ("--gpus", "--steps", "--warmup", "--impl", "--plan-only", "--workload", "--wide",
+                 "--batch-instances", "--no-cpu-baseline"):
+        assert flag in r.stdout, flag
