@@ -294,27 +294,39 @@ def run_batch(args):
     print(json.dumps(out), flush=True)
 
 
+def rank_context(torch, device_type="cuda"):
+    """(rank, world size, barrier, max over ranks) of the process group that torchrun's
+    environment describes: NCCL on GPUs, gloo on the CPU; a world of one needs no group.
+    Replicas exchange nothing but these two timing collectives."""
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world <= 1:
+        return rank, 1, (lambda: None), (lambda x: x)
+    import torch.distributed as dist
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = torch.device(f"cuda:{local}") if device_type == "cuda" else torch.device("cpu")
+    if not dist.is_initialized():
+        if device_type == "cuda":
+            dist.init_process_group("nccl", device_id=dev)
+        else:
+            dist.init_process_group("gloo")
+
+    def max_over_ranks(x):
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    return rank, world, (lambda: dist.barrier()), max_over_ranks
+
+
 def run_figaro(args):
     import torch
     from paper_2204_00525_gb300 import binding
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    rank, world, barrier, max_over_ranks = rank_context(torch, "cuda")
     torch.cuda.set_device(local)
     binding.load(build_if_missing=True)
-    barrier = (lambda: dist.barrier()) if dist else (lambda: None)
-
-    def max_over_ranks(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
 
     t0 = time.time()
     db = synth.path3(seed=2 + rank, rows=args.rows)
@@ -508,8 +520,9 @@ def run_figaro(args):
     }
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.sample_rows)
-    if dist:
-        dist.barrier()
+    if world > 1:
+        import torch.distributed as dist
+        barrier()
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
