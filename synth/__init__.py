@@ -326,3 +326,24 @@ CONFIGS = {
     "star_5m": lambda **kw: star(seed=3, **kw),
     "snowflake_10m": lambda **kw: snowflake(seed=4, **kw),
 }
+
+
+def presorted(db: Database) -> Database:
+    """A copy of ``db`` whose relations are stored in join-key order, the paper's input
+    convention (§5 assumes S_i sorted on X_i, a child first on the attributes it shares
+    with its parent; §9 times pre-sorted inputs): the attributes shared with the parent
+    first, then the relation's other key attributes, each part by ascending attribute id,
+    values ascending, ties in input order."""
+    rels = []
+    for i, r in enumerate(db.relations):
+        p = db.parent[i]
+        shared = sorted(set(r.key_attrs) & set(db.relations[p].key_attrs)) if p >= 0 else []
+        rest = sorted(set(r.key_attrs) - set(shared))
+        cols = [r.key_attrs.index(a) for a in shared + rest]
+        if cols:
+            order = np.lexsort(tuple(r.keys[:, c] for c in reversed(cols)))   # stable
+        else:
+            order = np.arange(r.n_rows)
+        rels.append(Relation(r.name, r.key_attrs, np.ascontiguousarray(r.keys[order]),
+                             np.ascontiguousarray(r.data[order])))
+    return Database(rels, list(db.parent), list(db.attr_names), db.description + " (pre-sorted)")
