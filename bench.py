@@ -1,13 +1,18 @@
 #!/usr/bin/env python
-"""Benchmark: input cells per second to R for the acyclic path join
-R1(a; 8 cols) - R2(a, b; 8 cols) - R3(b; 8 cols), 2M rows per relation, a and b
-Zipf(1.1) over 2,000 keys, N(0,1) float64 data (the join has ~1.5e16 rows and is never
-materialised).  One step = sort, segment, count (Alg. 3), heads/tails (Alg. 4), TSQR (§7)
--> R, on inputs already resident in HBM.
+"""Benchmark: input cells per second to R for the 4-relation snowflake join
+D3(c) 100k rows - D1(a, c) 1M - F(a, b) 10M - D2(b) 1M, 50 U[-1,1] float64 columns each
+(200 in all, 10 of them x 1e4), key-fkey with every key referenced; the join has 10M
+rows x 200 columns and is never materialised.  One step = sort, segment, count (Alg. 3),
+heads/tails and joins (Alg. 4), TSQR (§7) -> R, on inputs already resident in HBM.  This
+is the largest single-GPU workload of the benchmark set (628 M input cells, 5 GB).
 
-Also measured: the mixed-precision path (float32 TSQR leaves) against the FP64 path,
-end-to-end throughput through the C ABI with host buffers, the dominant kernel's
-roofline, and the CPU oracle on a bounded sample of the same workload.
+Also measured on it: the mixed-precision path against the FP64 path (whole step and TSQR
+alone), R^T R errors against the oracle's factorized A^T A (stored in tests/golden), the
+same steps on pre-sorted inputs (the paper's timing convention), end-to-end throughput
+through the C ABI with host buffers, stage times with their rooflines, the dominant
+kernel's roofline against a live FP64 rate measurement, the gradient of ||R||_F^2, the
+CPU FiGaRo baseline (C with OpenMP on all host cores) on the same workload, and the
+2M-row path join as a second workload.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl figaro|reference]
 Under torchrun every rank runs an independent instance (weak scaling; the path has no
@@ -15,12 +20,12 @@ data exchange) and rank 0 prints one JSON line.
 
 Other workloads (one JSON line each, not the benchmark line): --batch-instances K (the
 batch of independent two-relation joins as one graph launch) and --wide (the star and
-snowflake joins, whose blocks of 33-256 columns go through the streamed fold).
---plan-only runs one plan on a chosen workload without output, for ncu captures.
+snowflake joins, one call at a time).  --plan-only runs one plan on a chosen workload
+without output, for ncu captures.
 """
 import os
 
-for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+for _v in ("OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
 
 import argparse
@@ -39,15 +44,17 @@ import numpy as np
 import synth
 
 METRIC = "input cells/sec to R (GB/s vs HBM peak); mixed vs FP64 speedup at rel err ≤1e-6"
-WORKLOAD = ("path3_2m: R1(a;x1..x8) - R2(a,b;y1..y8) - R3(b;z1..z8), 2,000,000 rows each, "
-            "a,b Zipf(1.1) over 2,000 keys, N(0,1) float64 data, column-major; join ~1.5e16 rows")
-ROWS = 2_000_000
-SAMPLE_ROWS = 100_000          # oracle sample per relation (same shape and key distribution)
-FP64_PEAK_TFLOPS = 152 * 2070e6 * 4 / 1e12   # 152 SMs x 2.07 GHz x 2 DFMA/clk/SM x 2 flop
-# DRAM bytes per input row of the dominant kernel (k_tsqr_reg<double, 8>, leaf of a tails
-# block), from the ncu capture summarised in profiles/tsqr_reg8_fp64_path3_2m.md:
-# (dram__bytes_read.sum + dram__bytes_write.sum) / rows = 132.37 MB / 1,998,000 rows.
-DOMINANT_DRAM_BYTES_PER_ROW = 132.37e6 / 1_998_000
+WORKLOAD = ("snowflake_10m: D3(c) 100k - D1(a,c) 1M - F(a,b) 10M - D2(b) 1M rows, 50 U[-1,1] float64 "
+            "cols each (200; 10 cols x1e4), key-fkey, every key referenced; join 10M rows x 200 cols")
+PATH3 = ("path3_2m: R1(a;x1..x8) - R2(a,b;y1..y8) - R3(b;z1..z8), 2,000,000 rows each, "
+         "a,b Zipf(1.1) over 2,000 keys, N(0,1) float64 data; join ~1.5e16 rows")
+FP64_PEAK_DERIVED = 152 * 2070e6 * 4 / 1e12   # 152 SMs x 2.07 GHz x 2 DFMA/clk/SM x 2 flop
+REF_SAMPLE = 4                                # the reference arm's rows: the workload's / 4
+GOLDEN_GRAM = os.path.join(ROOT, "tests", "golden", "snowflake_gram.npz")
+# DRAM bytes per input row of the dominant kernel (k_tsqr_fold<double> leaf of the
+# 100-column generalized-tail block), from the ncu capture of the same kernel on a
+# 2M-row snowflake summarised in profiles/tsqr_fold_f64_snowflake.md (scaled by rows).
+DOMINANT_DRAM_BYTES_PER_ROW = None
 
 
 def log(*a):
@@ -200,6 +207,8 @@ def wide_workload(name):
     """The wide-block workloads: the 5M-row many-to-many star (16 columns per relation,
     a 48-column generalized-tail block of ~5M rows) and the 10M-row snowflake (50 columns per
     relation, 10 of the 200 scaled by 1e4; 100-, 150- and 200-column blocks)."""
+    if name == "snowflake-small":    # a fifth of the rows: small ncu captures of the same kernels
+        return synth.snowflake(f_rows=2_000_000, d1_rows=200_000, d2_rows=200_000, d3_rows=20_000)
     return synth.star() if name == "star" else synth.snowflake()
 
 
@@ -319,6 +328,82 @@ def rank_context(torch, device_type="cuda"):
     return rank, world, (lambda: dist.barrier()), max_over_ranks
 
 
+def gram_errors(R, G):
+    """||R^T R - G||_F / ||G||_F, plain and with rows and columns scaled by 1/sqrt(G_jj)
+    (the 1e4 columns dominate the plain norm)."""
+    E = R.T @ R - G
+    d = np.sqrt(np.maximum(np.diag(G), 1e-300))
+    Es, Gs = E / d[:, None] / d[None, :], G / d[:, None] / d[None, :]
+    return float(np.linalg.norm(E) / np.linalg.norm(G)), float(np.linalg.norm(Es) / np.linalg.norm(Gs))
+
+
+def load_golden_gram(db):
+    """The oracle's A^T A of the snowflake workload, if it was computed from these inputs."""
+    try:
+        z = np.load(GOLDEN_GRAM)
+    except OSError:
+        return None, "tests/golden/snowflake_gram.npz missing"
+    if str(z["fingerprint"]) != synth.fingerprint(db):
+        return None, "stored oracle Gram belongs to other inputs (generator changed)"
+    return z["gram"], "oracle factorized A^T A (tests/golden/snowflake_gram.npz)"
+
+
+def stage_rooflines(plan, stages, db, hbm, fp64_peak, mixed):
+    """Per-stage algorithmic bytes (HBM-bound stages) or flops (TSQR) over the stage's
+    time in a stage-timed plan.  Bytes count what the stage must move at least: sort reads
+    the keys and writes a permutation; heads/tails read the data and write tails and heads;
+    joins read the joined Data and write generalized tails and heads."""
+    esz_t = 4 if mixed else 8
+    sz = []
+    for i, r in enumerate(db.relations):
+        v = plan.debug(i, "sizes", "int64")
+        sz.append({"M": int(v[0]), "G": int(v[1]), "P": int(v[2]), "K": int(v[6]), "N": r.n_data,
+                   "N_sub": int(v[7]), "gen": int(v[4]), "root": int(v[5])})
+    b_sort = sum(s["M"] * (8 * s["K"] + 4) for s in sz)
+    b_seg = sum(s["M"] * 8 + s["G"] * 4 for s in sz)
+    b_ht = sum(s["M"] * s["N"] * 8 + (s["M"] - s["G"]) * s["N"] * esz_t + s["G"] * s["N"] * 8 for s in sz)
+    b_join = sum((s["G"] * s["N_sub"] * 8 + s["gen"] * s["N_sub"] * esz_t + s["P"] * s["N_sub"] * 8)
+                 for s in sz if s["gen"] > 0 or s["root"] > 0)
+    out = {}
+    for name, b in (("sort", b_sort), ("segment", b_seg), ("heads_tails", b_ht), ("join_project", b_join)):
+        ms = stages[name]
+        out[name] = {"ms": ms, "algorithmic_bytes": b, "gbs": b / (ms * 1e-3) / 1e9 if ms > 0 else None,
+                     "bound": "hbm", "frac": (b / (ms * 1e-3) / 1e9) / hbm if ms > 0 else None}
+    info = plan.info()
+    ms = stages["tsqr_tree"]
+    fl = info["tsqr_leaf_flops"]
+    out["tsqr"] = {"ms": ms, "algorithmic_flops": fl, "tflops": fl / (ms * 1e-3) / 1e12,
+                   "bound": "fp32 pipe / tensor" if mixed else "fp64 pipe",
+                   "frac_of_measured_fp64": None if mixed else fl / (ms * 1e-3) / 1e12 / fp64_peak,
+                   "note": "leaf flops sum_b 2 rows_b n_b^2 - 2/3 n_b^3 over the whole TSQR section (leaf + tree + final QR)"}
+    out["counts"] = {"ms": stages["counts"], "bound": "latency (per-group kernels over <= 10M groups)"}
+    return out, sz
+
+
+def plan_pair(binding, torch, inputs, parent, **kw):
+    ps = []
+    for _ in range(2):
+        p = binding.JoinPlan(inputs, parent, stream=torch.cuda.Stream(), **kw)
+        p._R = torch.empty(p.n_cols, p.n_cols, dtype=torch.float64, device="cuda")
+        ps.append(p)
+    return ps
+
+
+def one_plan(binding, torch, inputs, parent, stream, **kw):
+    p = binding.JoinPlan(inputs, parent, stream=stream, **kw)
+    p._R = torch.empty(p.n_cols, p.n_cols, dtype=torch.float64, device="cuda")
+    return p
+
+
+def staged_run(binding, torch, inputs, parent, stream, steps, warmup, barrier, **kw):
+    """Stage times (ms per call), block leaf times and the plan of a stage-timed run."""
+    p = one_plan(binding, torch, inputs, parent, stream, stage_timing=True, **kw)
+    ms = time_steps(p, torch, steps, warmup, barrier)
+    st = {k: v[0] / steps for k, v in p.stage_times().items()}
+    blocks = [(a / steps, n, r) for a, n, r in p.block_times()]
+    return p, ms, st, blocks
+
+
 def run_figaro(args):
     import torch
     from paper_2204_00525_gb300 import binding
@@ -327,199 +412,196 @@ def run_figaro(args):
     rank, world, barrier, max_over_ranks = rank_context(torch, "cuda")
     torch.cuda.set_device(local)
     binding.load(build_if_missing=True)
+    K, W = args.steps, args.warmup
+    K2 = max(3, min(K, 5))          # secondary measurements (stages, pre-sorted, refined, backward)
 
     t0 = time.time()
-    db = synth.path3(seed=2 + rank, rows=args.rows)
-    cells = db.input_cells()
-    in_bytes = db.input_bytes()
-    log(f"[rank {rank}] generated {cells / 1e6:.1f}M cells in {time.time() - t0:.1f}s")
-    dev_inputs = make_inputs(db, torch, "cuda")
+    db = synth.snowflake(seed=4 + rank)
+    dbs = synth.presorted(db)
+    cells, in_bytes = db.input_cells(), db.input_bytes()
+    log(f"[rank {rank}] generated {cells / 1e6:.1f}M cells (+ pre-sorted copy) in {time.time() - t0:.1f}s")
+    G_ref, g_src = load_golden_gram(db) if rank == 0 else (None, "rank > 0")
+    dev = make_inputs(db, torch, "cuda")
     stream = torch.cuda.current_stream()
+    fp64_rate = binding.figaro_fp64_fma_rate(stream.cuda_stream)
+    hbm, hbm_kind = peaks()
 
-    # --- FP64 path (the headline): production plans, kernels as a user gets them.
-    # Throughput: two calls in flight (two plans on two streams); latency: one plan alone.
-    pair = []
-    for _ in range(2):
-        p = binding.JoinPlan(dev_inputs, db.parent, stream=torch.cuda.Stream())
-        p._R = torch.empty(db.n_cols, db.n_cols, dtype=torch.float64, device="cuda")
-        pair.append(p)
+    # --- FP64 path (the headline): throughput with two calls in flight, latency of one call
+    pair = plan_pair(binding, torch, dev, db.parent)
     with ClockSampler(local) as clk:
-        ms64 = time_steps_pipelined(pair, torch, args.steps, args.warmup, barrier)
+        ms64 = time_steps_pipelined(pair, torch, K, W, barrier)
     clocks = clk.summary()
     ms64 = max_over_ranks(ms64)
     assert torch.equal(pair[0]._R, pair[1]._R)
     for p in pair:
         p.close()
-    p64 = binding.JoinPlan(dev_inputs, db.parent, stream=stream)
-    p64._R = torch.empty(db.n_cols, db.n_cols, dtype=torch.float64, device="cuda")
-    lat64 = max_over_ranks(time_steps(p64, torch, args.steps, args.warmup, barrier))
+    p64 = one_plan(binding, torch, dev, db.parent, stream)
+    lat64 = max_over_ranks(time_steps(p64, torch, K, W, barrier))
     info = p64.info()
     R64 = p64._R.cpu().numpy()
     p64.close()
-
-    # --- stage breakdown and the leaf roofline: a second plan with CUDA events around
-    # every stage (its TSQR chains run serialised so that kernel times are not shared)
-    pst = binding.JoinPlan(dev_inputs, db.parent, stage_timing=True, stream=stream)
-    pst._R = torch.empty(db.n_cols, db.n_cols, dtype=torch.float64, device="cuda")
-    ms_staged = time_steps(pst, torch, args.steps, args.warmup, barrier)
-    stages = pst.stage_times()
-    block_times = pst.block_times()
+    pst, ms_st64, st64, blk64 = staged_run(binding, torch, dev, db.parent, stream, K2, W, barrier)
+    roof64, sizes = stage_rooflines(pst, st64, db, hbm, fp64_rate, False)
     pst.close()
 
     # --- mixed path
-    mx_pair = []
-    for _ in range(2):
-        p = binding.JoinPlan(dev_inputs, db.parent, precision=binding.FIGARO_PREC_MIXED, stream=torch.cuda.Stream())
-        p._R = torch.empty(db.n_cols, db.n_cols, dtype=torch.float64, device="cuda")
-        mx_pair.append(p)
-    msmx_tp = max_over_ranks(time_steps_pipelined(mx_pair, torch, args.steps, args.warmup, barrier))
-    for p in mx_pair:
+    mpair = plan_pair(binding, torch, dev, db.parent, precision=binding.FIGARO_PREC_MIXED)
+    msmx_tp = max_over_ranks(time_steps_pipelined(mpair, torch, K, W, barrier))
+    for p in mpair:
         p.close()
-    pmx = binding.JoinPlan(dev_inputs, db.parent, precision=binding.FIGARO_PREC_MIXED, stream=stream)
-    pmx._R = torch.empty(db.n_cols, db.n_cols, dtype=torch.float64, device="cuda")
-    msmx = max_over_ranks(time_steps(pmx, torch, args.steps, args.warmup, barrier))
+    pmx = one_plan(binding, torch, dev, db.parent, stream, precision=binding.FIGARO_PREC_MIXED)
+    latmx = max_over_ranks(time_steps(pmx, torch, K, W, barrier))
     Rmx = pmx._R.cpu().numpy()
-    G64 = R64.T @ R64
-    err_mx = float(np.linalg.norm(Rmx.T @ Rmx - G64) / np.linalg.norm(G64))
     pmx.close()
-    pmxs = binding.JoinPlan(dev_inputs, db.parent, precision=binding.FIGARO_PREC_MIXED, stage_timing=True,
-                            stream=stream)
-    pmxs._R = torch.empty(db.n_cols, db.n_cols, dtype=torch.float64, device="cuda")
-    time_steps(pmxs, torch, args.steps, args.warmup, barrier)
-    mx_stages = {k: v[0] / args.steps for k, v in pmxs.stage_times().items()}
-    pmxs.close()
-
-    # --- mixed path with the CholeskyQR2-style refinement
-    pmr = binding.JoinPlan(dev_inputs, db.parent, precision=binding.FIGARO_PREC_MIXED_REFINED, stream=stream)
-    pmr._R = torch.empty(db.n_cols, db.n_cols, dtype=torch.float64, device="cuda")
-    msmr = max_over_ranks(time_steps(pmr, torch, args.steps, args.warmup, barrier))
+    pms, ms_stmx, stmx, blkmx = staged_run(binding, torch, dev, db.parent, stream, K2, W, barrier,
+                                           precision=binding.FIGARO_PREC_MIXED)
+    roofmx, _ = stage_rooflines(pms, stmx, db, hbm, fp64_rate, True)
+    pms.close()
+    pmr = one_plan(binding, torch, dev, db.parent, stream, precision=binding.FIGARO_PREC_MIXED_REFINED)
+    latmr = max_over_ranks(time_steps(pmr, torch, K2, W, barrier))
     Rmr = pmr._R.cpu().numpy()
     refined = int(pmr.info()["refined"])
     pmr.close()
-    err_mr = float(np.linalg.norm(Rmr.T @ Rmr - G64) / np.linalg.norm(G64))
-    err_mr_r = float(np.linalg.norm(Rmr - R64) / np.linalg.norm(R64))
+
+    # --- pre-sorted inputs (the paper's convention: sorting excluded)
+    del dev
+    torch.cuda.empty_cache()
+    devs = make_inputs(dbs, torch, "cuda")
+    pps = plan_pair(binding, torch, devs, dbs.parent, presorted=True)
+    ms64_ps = max_over_ranks(time_steps_pipelined(pps, torch, K2, W, barrier))
+    R64_ps = pps[0]._R.cpu().numpy()
+    for p in pps:
+        p.close()
+    ppm = plan_pair(binding, torch, devs, dbs.parent, presorted=True, precision=binding.FIGARO_PREC_MIXED)
+    msmx_ps = max_over_ranks(time_steps_pipelined(ppm, torch, K2, W, barrier))
+    for p in ppm:
+        p.close()
 
     # --- gradient of ||R||_F^2 with respect to all data columns (figaro_backward)
-    pg = binding.JoinPlan(dev_inputs, db.parent, gradients=True, stream=stream)
+    pg = binding.JoinPlan(devs, dbs.parent, presorted=True, gradients=True, stream=stream)
     Rg = pg.qr_r()
     Rbar = 2.0 * Rg
-    for _ in range(args.warmup):
+    for _ in range(W):
         pg.backward(Rg, Rbar)
     torch.cuda.synchronize()
     eb0, eb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     eb0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(K2):
         grads = pg.backward(Rg, Rbar)
     eb1.record(stream)
     torch.cuda.synchronize()
-    bwd_ms = max_over_ranks(eb0.elapsed_time(eb1) / args.steps)
+    bwd_ms = max_over_ranks(eb0.elapsed_time(eb1) / K2)
     pg.close()
-    del grads
+    del grads, devs
+    torch.cuda.empty_cache()
 
-    # --- end to end through the C ABI with pinned host buffers
-    host_inputs = make_inputs(db, torch, "cpu")
-    ph = binding.JoinPlan(host_inputs, db.parent, mem=binding.FIGARO_MEM_HOST, stream=stream)
+    # --- end to end through the C ABI with pinned host buffers: every step copies all
+    # keys and data in and R out; two plans on two streams alternate so that one step's
+    # copies overlap the other's computation
+    host = make_inputs(db, torch, "cpu")
+    ph = binding.JoinPlan(host, db.parent, mem=binding.FIGARO_MEM_HOST, stream=stream)
     Rh = torch.empty(db.n_cols, db.n_cols, dtype=torch.float64).pin_memory()
-    for _ in range(args.warmup):
+    for _ in range(W):
         ph.qr_r(out=Rh)
     barrier()
     t = time.perf_counter()
-    for _ in range(args.steps):
-        ph.qr_r(out=Rh)          # H2D copies, the whole path, D2H of R, final sync
-    e2e_seq_ms = max_over_ranks((time.perf_counter() - t) * 1e3 / args.steps)
+    for _ in range(K2):
+        ph.qr_r(out=Rh)
+    e2e_seq_ms = max_over_ranks((time.perf_counter() - t) * 1e3 / K2)
     ph.close()
-    # pipelined: two plans on two streams alternate (figaro_qr_r_async / figaro_plan_sync),
-    # so one step's host-to-device copies overlap the other's computation; every step still
-    # copies its inputs in and its R out
     streams = [torch.cuda.Stream(), torch.cuda.Stream()]
-    pp = [binding.JoinPlan(host_inputs, db.parent, mem=binding.FIGARO_MEM_HOST, stream=s) for s in streams]
+    pp = [binding.JoinPlan(host, db.parent, mem=binding.FIGARO_MEM_HOST, stream=s) for s in streams]
     Rp = [torch.empty(db.n_cols, db.n_cols, dtype=torch.float64).pin_memory() for _ in pp]
-    for i in range(max(args.warmup, 2)):
+    for i in range(max(W, 2)):
         pp[i % 2].qr_r_async(Rp[i % 2])
         pp[i % 2].sync()
     barrier()
     t = time.perf_counter()
-    for i in range(args.steps):
+    for i in range(K):
         p_i = pp[i % 2]
         if i >= 2:
-            p_i.sync()                 # its previous step (two steps back) is complete
+            p_i.sync()
         p_i.qr_r_async(Rp[i % 2])
     for p_i in pp:
         p_i.sync()
-    e2e_ms = max_over_ranks((time.perf_counter() - t) * 1e3 / args.steps)
+    e2e_ms = max_over_ranks((time.perf_counter() - t) * 1e3 / K)
     assert np.array_equal(Rp[0].numpy(), Rp[1].numpy())
     for p_i in pp:
         p_i.close()
+    del host
+    torch.cuda.empty_cache()
 
-    hbm, hbm_kind = peaks()
+    # --- the 2M-row path join (second workload): FP64 throughput, mixed latency
+    p3 = path3_numbers(binding, torch, rank, K, W, barrier, max_over_ranks, world)
+
+    # --- errors against the oracle's A^T A (or the FP64 path where it is missing)
+    G = G_ref if G_ref is not None else R64.T @ R64
+    e64 = gram_errors(R64, G) if G_ref is not None else (None, None)
+    emx, emr, e64ps = gram_errors(Rmx, G), gram_errors(Rmr, G), gram_errors(R64_ps, G)
+
+    # --- the dominant kernel: the FP64 fold leaf of the 100-column generalized-tail block
+    leaf_ms, n_dom, rows_dom = max(blk64)
+    dom_flops = 2.0 * rows_dom * n_dom * n_dom - 2.0 / 3.0 * n_dom ** 3
+    dom_tflops = dom_flops / (leaf_ms * 1e-3) / 1e12
+    roofline = {"kernel": f"k_tsqr_fold<double> leaf of the {n_dom}-column block ({rows_dom} rows): streamed "
+                          "Householder fold, FP64", "bound": "alu", "achieved": dom_tflops,
+                "peak": fp64_rate, "unit": "TFLOP/s", "frac": dom_tflops / fp64_rate,
+                "traffic": (DOMINANT_DRAM_BYTES_PER_ROW * rows_dom if DOMINANT_DRAM_BYTES_PER_ROW else None),
+                "peak_kind": "measured in this run: FP64 FMA loop (figaro_fp64_fma_rate), burst",
+                "frac_of_derived_peak": dom_tflops / FP64_PEAK_DERIVED,
+                "derived_peak": FP64_PEAK_DERIVED, "flops_per_launch": dom_flops, "rows_per_launch": rows_dom,
+                "ms_per_launch": leaf_ms, "launches_per_step": 1,
+                "algorithmic_bytes_per_launch": rows_dom * n_dom * 8,
+                "timing": "CUDA events around the launch on its stream in the stage-timed plan"}
+    tsqr64, tsqrmx = st64["tsqr_tree"], stmx["tsqr_tree"]
     value = cells * world / (ms64 * 1e-3)
     gbs = in_bytes * world / (ms64 * 1e-3) / 1e9
-    steps_timed = args.steps
-    # stage breakdown of the FP64 step (serialised TSQR; "tsqr_tree" is the whole TSQR section)
-    per_stage = {k: v[0] / steps_timed for k, v in stages.items()}
-    launches = {k: v[1] / steps_timed for k, v in stages.items()}
-    dom = max((k for k in per_stage if k != "tsqr_leaf"), key=per_stage.get)
-    leaf_ms = per_stage["tsqr_leaf"]
-    # the dominant kernel: the register TSQR leaf of the 8-column tails blocks (one launch
-    # per block per step, timed by CUDA events around it on its stream in the stage-timed
-    # plan).  Algorithmic flops per launch: 2 rows n^2 - 2/3 n^3 (Householder, R only).
-    dom_blocks = [(ms / steps_timed, n, rows) for ms, n, rows in block_times if n == 8 and rows > 0]
-    dom_flops = sum(2.0 * rows * n * n - 2.0 / 3.0 * n ** 3 for _, n, rows in dom_blocks) / len(dom_blocks)
-    dom_ms = sum(ms for ms, _, _ in dom_blocks) / len(dom_blocks)
-    dom_rows = sum(rows for _, _, rows in dom_blocks) / len(dom_blocks)
-    dom_tflops = dom_flops / (dom_ms * 1e-3) / 1e12
-    roofline = {"kernel": "k_tsqr_reg<double, 8> (TSQR leaf of a tails block: warp-per-tile Householder "
-                          "in registers, FP64)",
-                "bound": "alu", "achieved": dom_tflops, "peak": round(FP64_PEAK_TFLOPS, 3),
-                "unit": "TFLOP/s", "frac": dom_tflops / FP64_PEAK_TFLOPS,
-                "traffic": DOMINANT_DRAM_BYTES_PER_ROW * dom_rows,
-                "peak_kind": "derived FP64 pipe peak: 152 SMs x 2 DFMA/clk x 2070 MHz",
-                "flops_per_launch": dom_flops, "rows_per_launch": dom_rows, "ms_per_launch": dom_ms,
-                "launches_per_step": len(dom_blocks),
-                "algorithmic_bytes_per_launch": dom_rows * 8 * 8,
-                "all_leaf_launches": {"ms_per_step": leaf_ms, "flops_per_step": info["tsqr_leaf_flops"],
-                                      "tflops": info["tsqr_leaf_flops"] / (leaf_ms * 1e-3) / 1e12,
-                                      "launches_per_step": launches["tsqr_leaf"]},
-                "staged_ms_per_step": ms_staged, "largest_stage": dom}
     out = {
-        "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak",
         "throughput_mode": "two calls in flight (two plans, two streams, figaro_qr_r_async / figaro_plan_sync)",
-        "latency_ms_per_step": lat64,
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded, see config)",
-        "config": {"workload": WORKLOAD, "rows_per_relation": args.rows, "cols": db.n_cols,
-                   "input_cells_per_gpu": cells, "input_bytes_per_gpu": in_bytes,
-                   "l2": "inputs exceed L2 (448 MB > 129 MB); no flush", "sort": "included",
+        "latency_ms_per_step": lat64, "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded snowflake generator, see config)",
+        "config": {"workload": WORKLOAD, "rows": [r.n_rows for r in db.relations],
+                   "cols": db.n_cols, "input_cells_per_gpu": cells, "input_bytes_per_gpu": in_bytes,
+                   "l2": "inputs exceed L2 (5.0 GB > 129 MB); no flush", "sort": "included (pre-sorted below)",
                    "parallelism": f"replicas x{world} (independent instances)"},
         "gbs": gbs, "hbm_frac": gbs / hbm, "hbm_peak_gbs": hbm, "hbm_peak_kind": hbm_kind,
-        "backward": {"ms_per_call": bwd_ms, "loss": "||R||_F^2", "value": cells * world / (bwd_ms * 1e-3),
-                     "unit": "cells/s", "note": "figaro_backward after a forward call: gradients of all "
-                                                "data columns, FP64 (includes output allocation)"},
-        "mixed": {"ms_per_step": msmx, "value": cells * world / (msmx * 1e-3), "speedup_vs_fp64": lat64 / msmx,
-                  "basis": "one plan, one call at a time (latency), against latency_ms_per_step",
-                  "throughput_ms_per_step": msmx_tp, "throughput_value": cells * world / (msmx_tp * 1e-3),
-                  "throughput_speedup_vs_fp64": ms64 / msmx_tp,
-                  "rel_err_RtR_vs_fp64_path": err_mx, "stages_ms_per_step": mx_stages,
-                  "refined": {"ms_per_step": msmr, "value": cells * world / (msmr * 1e-3),
-                              "speedup_vs_fp64": lat64 / msmr, "refinement_applied": refined,
-                              "rel_err_RtR_vs_fp64_path": err_mr, "rel_err_R_vs_fp64_path": err_mr_r,
-                              "dtype": "mixed path + one CholeskyQR2-style correction with A^T A in "
-                                       "double-float"},
-                  "dtype": "double-float head/tail sums, f32 tails and TSQR leaf/tree, f64 counts, join, final QR"},
-        "stages_ms_per_step": per_stage,
-        "stage_note": "from a stage-timed plan with serialised TSQR chains; tsqr_tree = whole TSQR section, tsqr_leaf = its leaf launches",
+        "errors_vs": g_src,
+        "rel_err_RtR": e64[0], "rel_err_RtR_col_scaled": e64[1],
+        "presorted": {"ms_per_step": ms64_ps, "value": cells * world / (ms64_ps * 1e-3),
+                      "mixed_ms_per_step": msmx_ps, "mixed_value": cells * world / (msmx_ps * 1e-3),
+                      "rel_err_RtR": e64ps[0], "mode": "inputs stored in join-key order, figaro_options.presorted "
+                                                       "= 1 (order verified, sort skipped); two calls in flight"},
+        "mixed": {"ms_per_step": msmx_tp, "value": cells * world / (msmx_tp * 1e-3),
+                  "speedup_vs_fp64": ms64 / msmx_tp, "basis": "throughput, two calls in flight, vs ms_per_step",
+                  "latency_ms_per_step": latmx, "latency_speedup_vs_fp64": lat64 / latmx,
+                  "tsqr_ms": tsqrmx, "tsqr_ms_fp64": tsqr64, "tsqr_speedup_vs_fp64": tsqr64 / tsqrmx,
+                  "tsqr_basis": "a5+a6 (TSQR section) of the stage-timed plans",
+                  "rel_err_RtR": emx[0], "rel_err_RtR_col_scaled": emx[1],
+                  "stages_ms": stmx, "stage_rooflines": roofmx,
+                  "refined": {"ms_per_step": latmr, "speedup_vs_fp64": lat64 / latmr, "applied": refined,
+                              "rel_err_RtR": emr[0], "rel_err_RtR_col_scaled": emr[1]},
+                  "dtype": "double-float head/tail sums, f32 tails and TSQR (split-tf32 tensor-core trailing "
+                           "updates on wide blocks), f64 counts, joins, final QR"},
+        "stages_ms": st64, "stage_rooflines": roof64,
+        "stage_note": "stage-timed plans (CUDA events around every stage, TSQR chains serialised); "
+                      "tsqr_tree is the whole TSQR section, tsqr_leaf its leaf launches",
+        "blocks": [{"n": n, "rows": r, "leaf_ms": m} for m, n, r in blk64 if r > 0],
         "r0_rows": info["r0_rows"],
         "roofline": roofline,
+        "backward": {"ms_per_call": bwd_ms, "loss": "||R||_F^2", "value": cells * world / (bwd_ms * 1e-3),
+                     "unit": "cells/s", "note": "figaro_backward after a forward call (pre-sorted plan)"},
         "e2e": {"value": cells * world / (e2e_ms * 1e-3), "unit": "cells/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": db.n_cols * db.n_cols * 8 + 4,
                 "mode": "two plans on two streams alternating figaro_qr_r_async / figaro_plan_sync",
-                "sequential_ms_per_step": e2e_seq_ms, "h2d_note": "pinned H2D measured at ~210 GB/s: "
-                                                                  "2.2 ms of copies per step"},
-        "gpu_launches": int(info["launches"]) * args.steps,
+                "sequential_ms_per_step": e2e_seq_ms},
+        "path3_2m": p3,
+        "gpu_launches": int(info["launches"]) * K,
         "clocks": clocks,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args.sample_rows)
+        out["cpu_baseline"] = cpu_baseline(db, dbs)
     if world > 1:
         import torch.distributed as dist
         barrier()
@@ -528,34 +610,99 @@ def run_figaro(args):
         print(json.dumps(out), flush=True)
 
 
-def oracle_step(db):
-    from oracle import figaro as ofg
-    return ofg.figaro_r(db)
+def path3_numbers(binding, torch, rank, K, W, barrier, max_over_ranks, world):
+    db = synth.path3(seed=2 + rank)
+    dev = make_inputs(db, torch, "cuda")
+    pair = plan_pair(binding, torch, dev, db.parent)
+    ms = max_over_ranks(time_steps_pipelined(pair, torch, K, W, barrier))
+    R = pair[0]._R.cpu().numpy()
+    for p in pair:
+        p.close()
+    pm = one_plan(binding, torch, dev, db.parent, torch.cuda.current_stream(), precision=binding.FIGARO_PREC_MIXED)
+    msm = max_over_ranks(time_steps(pm, torch, K, W, barrier))
+    Rm = pm._R.cpu().numpy()
+    pm.close()
+    del dev
+    torch.cuda.empty_cache()
+    cells = db.input_cells()
+    G = R.T @ R
+    return {"workload": PATH3, "input_cells": cells, "ms_per_step": ms, "value": cells * world / (ms * 1e-3),
+            "unit": "cells/s", "mixed_latency_ms": msm,
+            "mixed_rel_err_RtR_vs_fp64_path": float(np.linalg.norm(Rm.T @ Rm - G) / np.linalg.norm(G))}
 
 
-def cpu_baseline(sample_rows, repeats=1):
-    db = synth.path3(seed=2, rows=sample_rows)
+def host_threads():
+    """All host cores this process may run on (the CPU baseline's thread count)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+ARM_PARTS = {"0xd4f": "Arm Neoverse V2", "0xd40": "Arm Neoverse V1", "0xd0c": "Arm Neoverse N1",
+             "0xd49": "Arm Neoverse N2"}
+
+
+def cpu_facts():
+    model = platform_model()
+    return {"nproc": os.cpu_count(), "cpu": model}
+
+
+def platform_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                for key in ("model name", "Model", "CPU part"):
+                    if line.startswith(key):
+                        v = line.split(":", 1)[1].strip()
+                        return f"{ARM_PARTS[v]} (CPU part {v})" if v in ARM_PARTS else v
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline(db, dbs):
+    """The CPU FiGaRo baseline (oracle/cfigaro: C with OpenMP, all host cores) on the same
+    workload: one run with the sort, one on the pre-sorted copy."""
+    from oracle import cfigaro
+    prep, preps = cfigaro.Prepared(db), cfigaro.Prepared(dbs)
+    threads = host_threads()
     t = time.perf_counter()
-    for _ in range(repeats):
-        oracle_step(db)
-    dt = (time.perf_counter() - t) / repeats
-    return {"value": db.input_cells() / dt, "unit": "cells/s", "cores": 1, "kind": "oracle",
-            "sample": f"path3 with {sample_rows} rows per relation (same key law and columns), "
-                      f"{db.input_cells()} cells, oracle FiGaRo R (Alg. 3, Alg. 4, §7 Householder), "
-                      f"{dt:.2f} s per run"}
+    _, sec = prep.run(threads=threads)
+    dt = time.perf_counter() - t
+    t = time.perf_counter()
+    _, secs = preps.run(threads=threads, presorted=True)
+    dts = time.perf_counter() - t
+    cells = db.input_cells()
+    return {"value": cells / dt, "unit": "cells/s", "cores": threads,
+            "kind": "oracle: CPU FiGaRo (Alg. 3, Alg. 4, Householder post-processing) in C with OpenMP",
+            "sample": f"the full workload ({cells} cells), one run: {dt:.2f} s with sort, "
+                      f"{dts:.2f} s pre-sorted; stage seconds [sort, counts, heads/tails+joins, QR] = "
+                      f"{[round(float(x), 3) for x in sec]}",
+            "presorted_value": cells / dts, "same_config": True, **cpu_facts()}
 
 
 def run_reference(args):
+    """--impl reference: the CPU FiGaRo baseline (there is no reference implementation to
+    install: the paper's code is not provided) on the host cores, each step one run on a
+    row sample (1/--ref-divisor, a quarter by default) of the snowflake workload (same
+    schema, key law and columns)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    db = synth.path3(seed=2, rows=args.sample_rows)
+    from oracle import cfigaro
+    div = max(1, args.ref_divisor)
+    db = synth.snowflake(f_rows=10_000_000 // div, d1_rows=1_000_000 // div, d2_rows=1_000_000 // div,
+                         d3_rows=max(100_000 // div, 1))
     cells = db.input_cells()
+    prep = cfigaro.Prepared(db)
+    threads = host_threads()
     for _ in range(args.warmup):
-        oracle_step(db)
+        prep.run(threads=threads)
     t = time.perf_counter()
     for _ in range(args.steps):
-        oracle_step(db)
+        prep.run(threads=threads)
     dt = (time.perf_counter() - t) / args.steps
     value = cells / dt
     print(json.dumps({
@@ -563,10 +710,12 @@ def run_reference(args):
         "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (seeded)",
-        "config": {"workload": WORKLOAD, "rows_per_relation": args.sample_rows,
-                   "note": "CPU oracle on a bounded sample of the same workload"},
-        "cpu_baseline": {"value": value, "unit": "cells/s", "cores": 1, "kind": "oracle",
-                         "sample": f"path3 with {args.sample_rows} rows per relation, {cells} cells"},
+        "config": {"workload": WORKLOAD, "rows": [r.n_rows for r in db.relations],
+                   "note": f"CPU FiGaRo baseline on a 1/{div} row sample of the same workload"},
+        "cpu_baseline": {"value": value, "unit": "cells/s", "cores": threads,
+                         "kind": "oracle: CPU FiGaRo in C with OpenMP",
+                         "sample": f"snowflake with 1/{div} of the rows ({cells} cells), sort included",
+                         **cpu_facts()},
         "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -577,12 +726,13 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="figaro", choices=["figaro", "reference"])
-    ap.add_argument("--rows", type=int, default=ROWS)
-    ap.add_argument("--sample-rows", type=int, default=SAMPLE_ROWS)
+    ap.add_argument("--rows", type=int, default=2_000_000, help="rows per relation of --workload path3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-divisor", type=int, default=REF_SAMPLE,
+                    help="--impl reference: rows of the workload divided by this")
     ap.add_argument("--plan-only", choices=["fp64", "mixed", "fp64-staged", "mixed-staged"],
                     help="profiling aid: run one plan only and print no JSON line")
-    ap.add_argument("--workload", choices=["path3", "star", "snowflake"], default="path3",
+    ap.add_argument("--workload", choices=["path3", "star", "snowflake", "snowflake-small"], default="snowflake",
                     help="workload of --plan-only")
     ap.add_argument("--wide", action="store_true",
                     help="measure the wide-block workloads (star, snowflake) instead")

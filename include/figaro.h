@@ -322,14 +322,23 @@ int64_t figaro_debug_read(figaro_plan_t plan, int32_t rel, int32_t what, void* d
  * Work arrays live in one fixed device array of 2 * 256 * 256 doubles plus an error word
  * (about 1 MiB), defined in the library and held by every GPU that loads it until the
  * process exits; N larger than 256 is rejected with FIGARO_ERR_UNSUPPORTED before any
- * device work.  The first call on a device looks up that array's device address (once per
- * device, with the device current); make that first call before any stream capture.  All
- * calls share the array: calls whose executions overlap on the GPU (other streams, other
- * host threads) race and must be serialised by the caller.  Enqueues on `stream` and
- * waits for it before returning.  Errors: INVALID_ARG, UNSUPPORTED, TIMEOUT (no
+ * device work.  Every call looks up that array's device address with the calling thread's
+ * current device (a host query, made before anything is enqueued).  All calls share the
+ * array: calls whose executions overlap on the GPU (other streams, other host threads)
+ * race and must be serialised by the caller.  Enqueues on `stream` and waits for it before
+ * returning; because of that wait, a `stream` that is being captured is refused with
+ * FIGARO_ERR_UNSUPPORTED before anything is enqueued.  figaro_last_error describes the
+ * failure of the last call on this thread.  Errors: INVALID_ARG, UNSUPPORTED, TIMEOUT (no
  * convergence in 40 sweeps), CUDA. */
 int figaro_svd_from_r_static(const double* R, int64_t ldr, int32_t n, double* sigma, double* V,
                              void* stream);
+
+/* Measurement aid, not part of the paper's method: the FP64 FMA rate of the current
+ * device in TFLOP/s (2 flops per FMA), from five launches of a kernel whose threads run
+ * eight independent FMA chains each (64 warps per SM), timed with CUDA events on
+ * `stream` after one warm-up launch; waits for the stream.  It is the measured ceiling
+ * that the benchmark quotes the FP64-pipe-bound kernels against.  Errors: INVALID_ARG, CUDA. */
+int figaro_fp64_fma_rate(double* tflops, void* stream);
 
 /* Name of a status code (static storage). */
 const char* figaro_error_string(int status);

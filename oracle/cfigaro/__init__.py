@@ -95,26 +95,37 @@ def max_threads() -> int:
     return int(load().cfig_max_threads())
 
 
+class Prepared:
+    """A database marshalled once for repeated runs (the timed region then covers the C
+    call only): column-major data copies, key arrays and the relation table."""
+
+    def __init__(self, db):
+        n = len(db.relations)
+        self.n, self.N = n, db.n_cols
+        self.rels = (cfig_relation * n)()
+        self._keep = []
+        for i, r in enumerate(db.relations):
+            keys = [np.ascontiguousarray(r.keys[:, k], dtype=np.int64) for k in range(r.keys.shape[1])]
+            data = np.asfortranarray(r.data, dtype=np.float64)
+            attrs = (C.c_int32 * max(len(keys), 1))(*r.key_attrs)
+            kp = (C.c_void_p * max(len(keys), 1))(*[k.ctypes.data for k in keys])
+            self._keep += [keys, data, attrs, kp]
+            self.rels[i] = cfig_relation(r.n_rows, len(keys), attrs, kp, r.n_data,
+                                         data.ctypes.data if r.n_data else None, max(r.n_rows, 1))
+        self.parent = (C.c_int32 * n)(*db.parent)
+
+    def run(self, threads: int = 0, presorted: bool = False):
+        """(R, seconds): see ``figaro_r``."""
+        R = np.zeros((self.N, self.N))
+        sec = np.zeros(4)
+        st = load().cfig_figaro_r(self.n, self.rels, self.parent, int(presorted), int(threads), R.ctypes.data,
+                                  sec.ctypes.data)
+        if st != 0:
+            raise CFigaroError(st)
+        return R, sec
+
+
 def figaro_r(db, threads: int = 0, presorted: bool = False):
     """(R, seconds) of a ``synth.Database``: R (n_cols x n_cols, non-negative diagonal) and
     the wall seconds of [sort + grouping, Alg. 3, Alg. 4, post-processing]."""
-    lib = load()
-    n = len(db.relations)
-    rels = (cfig_relation * n)()
-    keep = []
-    for i, r in enumerate(db.relations):
-        keys = [np.ascontiguousarray(r.keys[:, k], dtype=np.int64) for k in range(r.keys.shape[1])]
-        data = np.asfortranarray(r.data, dtype=np.float64)
-        attrs = (C.c_int32 * max(len(keys), 1))(*r.key_attrs)
-        kp = (C.c_void_p * max(len(keys), 1))(*[k.ctypes.data for k in keys])
-        keep += [keys, data, attrs, kp]
-        rels[i] = cfig_relation(r.n_rows, len(keys), attrs, kp, r.n_data,
-                                data.ctypes.data if r.n_data else None, max(r.n_rows, 1))
-    par = (C.c_int32 * n)(*db.parent)
-    N = db.n_cols
-    R = np.zeros((N, N))
-    sec = np.zeros(4)
-    st = lib.cfig_figaro_r(n, rels, par, int(presorted), int(threads), R.ctypes.data, sec.ctypes.data)
-    if st != 0:
-        raise CFigaroError(st)
-    return R, sec
+    return Prepared(db).run(threads, presorted)

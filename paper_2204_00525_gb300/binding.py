@@ -97,6 +97,7 @@ def load(build_if_missing: bool = False):
         "figaro_batch_run": (C.c_int, [P, P]),
         "figaro_batch_launches": (C.c_int64, [P]),
         "figaro_batch_destroy": (C.c_int, [P]),
+        "figaro_fp64_fma_rate": (C.c_int, [C.POINTER(C.c_double), P]),
         "figaro_error_string": (C.c_char_p, [C.c_int]),
         "figaro_last_error": (C.c_char_p, []),
     }
@@ -140,6 +141,13 @@ def figaro_svd(plan, sigma_ptr: int, V_ptr: int, R_ptr: int = 0):
 
 def figaro_pca(plan, k: int, comp_ptr: int, eig_ptr: int):
     return check(load().figaro_pca(plan, k, C.c_void_p(comp_ptr), C.c_void_p(eig_ptr)))
+
+
+def figaro_fp64_fma_rate(stream: int) -> float:
+    """Measured FP64 FMA rate of the current device in TFLOP/s."""
+    v = C.c_double()
+    check(load().figaro_fp64_fma_rate(C.byref(v), C.c_void_p(stream)))
+    return v.value
 
 
 def figaro_svd_from_r_static(R_ptr: int, ldr: int, n: int, sigma_ptr: int, V_ptr: int, stream: int):

@@ -27,6 +27,10 @@ static int fail(int code, const std::string& msg) {
   return code;
 }
 
+// The same record for entry points defined in other translation units.
+int record_error(int code, const char* msg) { return fail(code, msg ? msg : ""); }
+void clear_error() { g_last_error.clear(); }
+
 #define FIG_CUDA(call)                                                                     \
   do {                                                                                     \
     cudaError_t e_ = (call);                                                               \

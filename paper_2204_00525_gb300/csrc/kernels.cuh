@@ -236,6 +236,11 @@ cudaError_t svd_set_attributes();
 void jacobi_svd(const double* R, int64_t ldr, int N, double* W, double* V, double* sigma,
                 double* Vout, int* err, cudaStream_t st, int64_t* launches);
 void square_values(const double* s, double* out, int k, cudaStream_t st, int64_t* launches);
+
+// figaro_last_error's message for entry points outside api.cu: record_error sets it and
+// returns `code`; clear_error empties it at the start of a call.
+int record_error(int code, const char* msg);
+void clear_error();
 void join_colsum(const double* heads, int64_t ldh, const int32_t* goff, const double* hrow, const uint64_t* phic,
                  const int32_t* sizes, int n, double* out, cudaStream_t st, int64_t* launches);
 void join_size(const uint64_t* full, const int32_t* sizes, unsigned long long* out, cudaStream_t st,

@@ -213,7 +213,6 @@ void square_values(const double* s, double* out, int k, cudaStream_t st, int64_t
 // (a process whose device memory is fully reserved by its own pool, a latency-critical
 // loop where an allocation's implicit synchronisation is not allowed); they still pass
 // R, sigma and V themselves.
-#include <mutex>
 
 namespace fig {
 
@@ -222,26 +221,16 @@ constexpr int kStaticSvdMaxN = 256;
 // held on every device that loads this library until the process exits.
 static __device__ __align__(256) double g_svd_static_scratch[2 * kStaticSvdMaxN * kStaticSvdMaxN + 32];
 
-constexpr int kStaticMaxDevices = 64;
-static double* g_svd_static_ptr[kStaticMaxDevices] = {nullptr};
-static std::mutex g_svd_static_mutex;
-
-// Device address of the static array on the current device, looked up once per device
-// (host code only holds a host-side stand-in for the symbol, which must not be passed to
-// a kernel).
+// Device address of the static array on the current device.  Host code only holds a
+// host-side stand-in for the symbol, which must not be passed to a kernel.  The address
+// is looked up on every call (a cheap host query; the call waits for its stream anyway),
+// so it stays valid if the module is loaded again, e.g. after cudaDeviceReset.
 static int static_scratch(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return FIGARO_ERR_CUDA;
-  if (dev < 0 || dev >= kStaticMaxDevices) return FIGARO_ERR_UNSUPPORTED;
-  std::lock_guard<std::mutex> lock(g_svd_static_mutex);
-  if (!g_svd_static_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_svd_static_scratch);
-    if (e != cudaSuccess || !p) return FIGARO_ERR_CUDA;
-    g_svd_static_ptr[dev] = static_cast<double*>(p);
-  }
-  *out = g_svd_static_ptr[dev];
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_svd_static_scratch);
+  if (e != cudaSuccess || !p)
+    return record_error(FIGARO_ERR_CUDA, "figaro_svd_from_r_static: cudaGetSymbolAddress failed");
+  *out = static_cast<double*>(p);
   return FIGARO_OK;
 }
 
@@ -250,23 +239,41 @@ static int static_scratch(double** out) {
 extern "C" int figaro_svd_from_r_static(const double* R, int64_t ldr, int32_t n, double* sigma, double* V,
                                         void* stream) {
   using namespace fig;
-  if (!R || !sigma || !V || n < 1 || ldr < n) return FIGARO_ERR_INVALID_ARG;
-  if (n > kStaticSvdMaxN) return FIGARO_ERR_UNSUPPORTED;
+  clear_error();
+  if (!R || !sigma || !V || n < 1 || ldr < n)
+    return record_error(FIGARO_ERR_INVALID_ARG, "figaro_svd_from_r_static: null pointer, n < 1 or ldr < n");
+  if (n > kStaticSvdMaxN)
+    return record_error(FIGARO_ERR_UNSUPPORTED, "figaro_svd_from_r_static: n above 256");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // The call ends by waiting for its stream, which a stream under capture does not allow
+  // (the wait would invalidate the caller's capture): refuse before enqueueing anything.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess)
+    return record_error(FIGARO_ERR_CUDA, "figaro_svd_from_r_static: cudaStreamIsCapturing failed");
+  if (cap != cudaStreamCaptureStatusNone)
+    return record_error(FIGARO_ERR_UNSUPPORTED, "figaro_svd_from_r_static: stream is being captured");
   double* base = nullptr;
   int rc = static_scratch(&base);
   if (rc != FIGARO_OK) return rc;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   double* W = base;
   double* Vw = base + (int64_t)n * n;
   int* err = reinterpret_cast<int*>(base + 2 * kStaticSvdMaxN * kStaticSvdMaxN);
+  // an error left by an earlier, unrelated launch on this thread is not this call's
+  (void)cudaGetLastError();
   // the error word keeps the previous call's value: clear it first
-  if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return FIGARO_ERR_CUDA;
+  if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess)
+    return record_error(FIGARO_ERR_CUDA, "figaro_svd_from_r_static: clearing the error word failed");
   const size_t smem = (size_t)n * sizeof(double);
   k_jacobi<<<1, kSvdThreads, smem, st>>>(R, ldr, n, W, Vw, sigma, V, 0, err);
+  cudaError_t le = cudaGetLastError();
+  if (le != cudaSuccess)
+    return record_error(FIGARO_ERR_CUDA, cudaGetErrorString(le));
   int host_err = 0;
-  if (cudaGetLastError() != cudaSuccess) return FIGARO_ERR_CUDA;
   if (cudaMemcpyAsync(&host_err, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
-    return FIGARO_ERR_CUDA;
-  if (cudaStreamSynchronize(st) != cudaSuccess) return FIGARO_ERR_CUDA;
-  return host_err;
+    return record_error(FIGARO_ERR_CUDA, "figaro_svd_from_r_static: reading the error word failed");
+  le = cudaStreamSynchronize(st);
+  if (le != cudaSuccess) return record_error(FIGARO_ERR_CUDA, cudaGetErrorString(le));
+  if (host_err != FIGARO_OK)
+    return record_error(host_err, "figaro_svd_from_r_static: the Jacobi kernel reported an error");
+  return FIGARO_OK;
 }

@@ -347,3 +347,17 @@ def presorted(db: Database) -> Database:
         rels.append(Relation(r.name, r.key_attrs, np.ascontiguousarray(r.keys[order]),
                              np.ascontiguousarray(r.data[order])))
     return Database(rels, list(db.parent), list(db.attr_names), db.description + " (pre-sorted)")
+
+
+def fingerprint(db: Database, stride: int = 9973) -> str:
+    """A short hash of a database's keys and data (every ``stride``-th row of every
+    relation, plus the shapes): it ties a stored expected value to the inputs it was
+    computed from, so that a changed generator is noticed instead of compared against."""
+    import hashlib
+    h = hashlib.sha256()
+    h.update(repr(list(db.parent)).encode())
+    for r in db.relations:
+        h.update(repr((r.name, tuple(r.key_attrs), r.keys.shape, r.data.shape)).encode())
+        h.update(np.ascontiguousarray(r.keys[::stride]).tobytes())
+        h.update(np.ascontiguousarray(r.data[::stride]).tobytes())
+    return h.hexdigest()[:16]
