@@ -43,9 +43,9 @@ enum figaro_status {
                                    the relations holding an attribute must be connected),
                                    or a key attribute occurs in a single relation         */
   FIGARO_ERR_NOT_REDUCED = 3,   /* require_reduced was set and a tuple does not join     */
-  FIGARO_ERR_OVERFLOW = 4,      /* a join count (§5) does not fit in 64 bits              */
+  FIGARO_ERR_OVERFLOW = 4,      /* a join count (§5) exceeds 2^64 - 1 (unsigned 64 bits)  */
   FIGARO_ERR_NOMEM = 5,         /* device or host allocation failed                      */
-  FIGARO_ERR_TIMEOUT = 6,       /* reserved for bounded device waits                     */
+  FIGARO_ERR_TIMEOUT = 6,       /* an iteration limit was reached (Jacobi sweeps)         */
   FIGARO_ERR_CUDA = 7,          /* a CUDA runtime call failed (see figaro_last_error)     */
   FIGARO_ERR_KEY_RANGE = 8,     /* a key value lies outside the range seen by figaro_plan */
   FIGARO_ERR_NOT_SORTED = 9,    /* presorted was set but a relation is not sorted         */
@@ -118,7 +118,14 @@ typedef struct figaro_join_tree {
  *                    of blocks with <= 16 columns by per-thread Givens rotations on
  *                    32-row chunks, skipping exact zeros (the paper's THIN flavour, for
  *                    very sparse blocks; wider blocks keep Householder), in float64 on
- *                    both precisions.                                                  */
+ *                    both precisions.
+ *   workspace_limit_mib  0 (default): no limit; otherwise figaro_plan fails with
+ *                    FIGARO_ERR_NOMEM, allocating nothing, when the plan's device workspace
+ *                    would exceed this many MiB (a memory budget for callers that share
+ *                    the device).
+ *   svd_max_sweeps   0 (default): 40; otherwise the largest number of Jacobi sweeps of
+ *                    figaro_svd / figaro_pca / figaro_pca_centered before they give up
+ *                    with FIGARO_ERR_TIMEOUT (not converged).                           */
 typedef struct figaro_options {
   int32_t precision;
   int32_t presorted;
@@ -127,7 +134,9 @@ typedef struct figaro_options {
   int32_t stage_timing;
   int32_t gradients;
   int32_t leaf;
-  int32_t reserved[9];
+  int32_t workspace_limit_mib;
+  int32_t svd_max_sweeps;
+  int32_t reserved[7];
 } figaro_options;
 
 typedef struct figaro_plan_s* figaro_plan_t;
@@ -303,7 +312,10 @@ int figaro_block_times(figaro_plan_t plan, int32_t max, double* leaf_ms, int32_t
  *                        the projection (internal non-root relations)
  *   FIGARO_DBG_DATA      float64[P x N_sub] column-major: the generalized heads
  *                        passed to the parent (internal non-root relations)
- *   FIGARO_DBG_ROOT_ROWS float64[G x N] column-major: the root's Data rows        */
+ *   FIGARO_DBG_ROOT_ROWS float64[G x N] column-major: the root's Data rows
+ * TAILS and GEN_TAILS hold the float64 rows of FIGARO_PREC_FP64 plans; mixed plans keep
+ * their tail rows in float32 (GEN_TAILS of FIGARO_PREC_MIXED_REFINED plans stay float64)
+ * and those arrays are not read by them.                                              */
 enum {
   FIGARO_DBG_SIZES = 0, FIGARO_DBG_PERM = 1, FIGARO_DBG_GROUP_OFF = 2, FIGARO_DBG_COUNTS = 3,
   FIGARO_DBG_PCOUNTS = 4, FIGARO_DBG_TAILS = 5, FIGARO_DBG_HEADS = 6, FIGARO_DBG_GEN_TAILS = 7,

@@ -52,6 +52,12 @@ struct Node {
   const double* data = nullptr;         // as given by the caller
   std::vector<void*> dkey;              // device copies (host-memory mode)
   double* ddata = nullptr;              // device copy (host-memory mode)
+  double* rowin = nullptr;              // row-major copy of the data for the sorted gather
+  double* crow = nullptr;               // row-major copy of the table passed to the parent
+  int crow_pitch = 0;
+  float* gtails32 = nullptr;            // mixed path (not refined): float generalized tails
+  double* jdata = nullptr;              // joined Data of process_and_join_children (internal)
+  int64_t ldj = 0;
   // packing: X_p attributes (ascending id) in the high bits, then the rest
   std::vector<int> pack_attr, pack_col, shift;
   int bits = 0, rest_bits = 0;
@@ -225,7 +231,18 @@ static void layout(figaro_plan_s& P, Arena& a) {
     if (!n.leaf && !n.root) {
       b.data2 = a.take<double>(M * n.N_sub);
       b.gtails = a.take<double>(M * n.N_sub);
+      n.gtails32 = (mixed && !refine) ? a.take<float>(M * n.N_sub) : nullptr;
+      n.ldj = (M + 7) & ~int64_t(7);
+      n.jdata = a.take<double>(n.ldj * std::max(n.N_sub, 1));
     }
+    if (!n.root) {                        // the parent gathers whole rows of this table
+      n.crow_pitch = row_pitch(std::max(n.leaf ? n.N : n.N_sub, 1));
+      n.crow = a.take<double>(M * n.crow_pitch);
+    }
+    // the sorted copy of a large table is gathered by whole rows: column-major data gets a
+    // row-major copy first
+    n.rowin = (!P.opt.presorted && n.layout == FIGARO_COL_MAJOR && row_gather_pays(M, n.N))
+                  ? a.take<double>(M * row_pitch(n.N)) : nullptr;
     if (n.root) b.rootrows = a.take<double>(M * n.N_sub);
     n.n_tiles = ht_tiles(M);
     const int wide = std::max(std::max(n.N, n.N_sub), 1);
@@ -590,6 +607,7 @@ static void bind_blocks(figaro_plan_s& P) {
     }
     if (!n.leaf && !n.root && n.N_sub > 0) {
       P.blocks[bi].ptr = n.b.gtails;
+      P.blocks[bi].ptr32 = n.gtails32;
       P.blocks[bi].ld = n.M;
       P.blocks[bi].sizes = n.b.sizes;
       ++bi;
@@ -815,6 +833,15 @@ static int enqueue_r(figaro_plan_s& P, double* R, int64_t ldr) {
     lp.lflag = n.b.lflag;
     lp.lsum = n.b.lsum;
     lp.n_tiles = n.n_tiles;
+    if (n.b.sperm && row_gather_pays(n.M, n.N)) {   // the sorted copy, by whole rows
+      if (n.layout == FIGARO_COL_MAJOR) {
+        rows_of(lp.data, n.ld, n.M, nullptr, n.N, n.rowin, row_pitch(n.N), s, &P.launches);
+        rows_gather(n.rowin, row_pitch(n.N), n.b.sperm, n.M, n.N, n.b.sdata, n.b.lds, s, &P.launches);
+      } else {
+        rows_gather(lp.data, n.ld, n.b.sperm, n.M, n.N, n.b.sdata, n.b.lds, s, &P.launches);
+      }
+      lp.sorted_ready = 1;
+    }
     leaf_heads_tails(lp, n.b.sizes, s, &P.launches);
     FIG_CUDA(rec(P.ev_leaf[i], s));
     if (!serial && n.blk_tails >= 0) {
@@ -844,11 +871,20 @@ static int enqueue_r(figaro_plan_s& P, double* R, int64_t ldr) {
     gp.hf = n.b.hf;
     gp.q = n.b.q;
     for (int j = 0; j < gp.n_child; ++j) {
+      Node& c = P.nodes[n.children[j]];
       gp.cdata[j] = n.link[j].data;
       gp.cld[j] = n.link[j].ld;
+      // whole rows of the child's table are gathered from a row-major copy of it
+      rows_of(n.link[j].data, n.link[j].ld, c.M, c.b.sizes + 1, c.leaf ? c.N : c.N_sub, c.crow, c.crow_pitch, st,
+              &P.launches);
+      gp.crow[j] = c.crow;
+      gp.cnp[j] = c.crow_pitch;
     }
+    gp.jdata = n.jdata;
+    gp.ldj = n.ldj;
     gp.coldesc = n.b.coldesc;
     gp.gtails = n.b.gtails;
+    gp.gtails32 = n.gtails32;
     gp.data2 = n.b.data2;
     gp.rootrows = n.b.rootrows;
     gp.tflag = n.b.tflag;
@@ -1056,6 +1092,10 @@ int figaro_plan(const figaro_join_tree* tree, const figaro_options* opt, void* s
     delete P;
     return fail(FIGARO_ERR_INVALID_ARG, "mem");
   }
+  if (P->opt.workspace_limit_mib < 0 || P->opt.svd_max_sweeps < 0) {
+    delete P;
+    return fail(FIGARO_ERR_INVALID_ARG, "workspace_limit_mib or svd_max_sweeps negative");
+  }
   P->st = static_cast<cudaStream_t>(stream);
   int rc = build(*P, tree);
   if (rc == FIGARO_OK) {
@@ -1080,6 +1120,12 @@ int figaro_plan(const figaro_join_tree* tree, const figaro_options* opt, void* s
   Arena measure;
   layout(*P, measure);
   P->arena_bytes = measure.off + 256;
+  if (P->opt.workspace_limit_mib > 0 && P->arena_bytes > ((size_t)P->opt.workspace_limit_mib << 20)) {
+    const size_t need = P->arena_bytes;
+    P->arena_bytes = 0;
+    figaro_plan_destroy(P);
+    return fail(FIGARO_ERR_NOMEM, "device workspace of " + std::to_string(need) + " bytes exceeds workspace_limit_mib");
+  }
   if (cudaMalloc(&P->arena, P->arena_bytes) != cudaSuccess) {
     cudaGetLastError();
     P->arena = nullptr;
@@ -1207,7 +1253,7 @@ static int run_svd(figaro_plan_s& P, double* R_out) {
   if (rc != FIGARO_OK) return rc;
   StageClock clk(P);
   clk.start(7);
-  jacobi_svd(P.Rtmp, P.N, P.N, P.svdW, P.svdV, P.sig, P.Vtmp, P.err_dev, P.st, &P.launches);
+  jacobi_svd(P.Rtmp, P.N, P.N, P.svdW, P.svdV, P.sig, P.Vtmp, P.err_dev, P.st, &P.launches, P.opt.svd_max_sweeps);
   clk.stop();
   if (R_out) {
     const bool host = P.opt.mem == FIGARO_MEM_HOST;
@@ -1316,7 +1362,7 @@ int figaro_batch_create(int32_t n, const figaro_plan_t* plans, double* const* R,
     rc = enqueue_r(P, P.Rtmp, P.N);
     const int ki = k ? k[i] : 0;
     if (rc == FIGARO_OK && ki > 0) {
-      jacobi_svd(P.Rtmp, P.N, P.N, P.svdW, P.svdV, P.sig, P.Vtmp, P.err_dev, P.exec, &B->launches);
+      jacobi_svd(P.Rtmp, P.N, P.N, P.svdW, P.svdV, P.sig, P.Vtmp, P.err_dev, P.exec, &B->launches, P.opt.svd_max_sweeps);
       e = cudaMemcpy2DAsync(components[i], ki * sizeof(double), P.Vtmp, P.N * sizeof(double), ki * sizeof(double),
                             P.N, cudaMemcpyDeviceToDevice, P.exec);
       if (e == cudaSuccess) square_values(P.sig, eigvals[i], ki, P.exec, &B->launches);
@@ -1424,7 +1470,7 @@ int figaro_project(figaro_plan_t p, int32_t mode, const double* R, int64_t ldr, 
     if (mode == FIGARO_PROJ_Q) {
       tri_inverse(R, ldr, N, P.scatter, P.err_dev, st);
     } else {
-      jacobi_svd(R, ldr, N, P.svdW, P.svdV, P.sig, P.Vtmp, P.err_dev, st, &P.launches);
+      jacobi_svd(R, ldr, N, P.svdW, P.svdV, P.sig, P.Vtmp, P.err_dev, st, &P.launches, P.opt.svd_max_sweeps);
       scale_v(P.Vtmp, P.sig, N, k, mode == FIGARO_PROJ_U, P.scatter, P.err_dev, st);
     }
     Xd = P.scatter;
@@ -1496,7 +1542,7 @@ int figaro_pca_centered(figaro_plan_t p, int32_t k, double* components, double* 
     join_colsum(n.b.heads, n.M, n.b.goff, n.b.hrow, n.b.phic, n.b.sizes, n.N, P.colsum + n.col_off, st, &P.launches);
   join_size(P.nodes[P.root].b.full, P.nodes[P.root].b.sizes, P.jsize, st, &P.launches);
   center_gram(P.Rtmp, P.N, P.colsum, P.jsize, P.scatter, st, &P.launches);
-  jacobi_svd(P.scatter, P.N, P.N, P.svdW, P.svdV, P.sig, P.Vtmp, P.err_dev, st, &P.launches);
+  jacobi_svd(P.scatter, P.N, P.N, P.svdW, P.svdV, P.sig, P.Vtmp, P.err_dev, st, &P.launches, P.opt.svd_max_sweeps);
   const bool host = P.opt.mem == FIGARO_MEM_HOST;
   const cudaMemcpyKind kind = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   FIG_CUDA(cudaMemcpy2DAsync(components, k * sizeof(double), P.Vtmp, P.N * sizeof(double), k * sizeof(double), P.N,

@@ -107,6 +107,80 @@ __global__ void __launch_bounds__(kCarryThreads) k_tile_carry(const uint8_t* tfl
   }
 }
 
+// ------------------------------------------------------------------ whole-row gathers
+// A row of a column-major table taken at a random position costs one 32-byte sector per
+// value, of which 8 bytes are used, and with tables larger than L2 those sectors come from
+// HBM.  The gathers below move whole rows instead: a row-major copy of the table (32 x 32
+// tiles through shared memory, coalesced on both sides), then every warp reads whole rows
+// (contiguous across the lanes) into a shared tile that is written out as column segments
+// of 32 consecutive rows.
+__global__ void __launch_bounds__(256) k_rows_of(const double* src, int64_t ld, int64_t bound, const int32_t* live,
+                                                 int cols, double* dst, int np) {
+  __shared__ double tile[32][33];
+  const int64_t rows = live ? (int64_t)live[0] : bound;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int ctiles = (cols + 31) >> 5;
+  const int64_t tiles = ((rows + 31) >> 5) * ctiles;
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int64_t r0 = (t / ctiles) * 32;
+    const int c0 = (int)(t % ctiles) * 32;
+    for (int k = ty; k < 32; k += 8) {              // tile[column][row]
+      const int c = c0 + k;
+      const int64_t r = r0 + tx;
+      tile[k][tx] = (c < cols && r < rows) ? src[(int64_t)c * ld + r] : 0.0;
+    }
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+      const int64_t r = r0 + k;
+      const int c = c0 + tx;
+      if (r < rows && c < cols) dst[r * np + c] = tile[tx][k];
+    }
+    __syncthreads();
+  }
+}
+
+void rows_of(const double* src, int64_t ld, int64_t bound, const int32_t* live, int cols, double* dst, int np,
+             cudaStream_t st, int64_t* launches) {
+  if (cols <= 0 || bound <= 0) return;
+  const int64_t tiles = ((bound + 31) / 32) * ((cols + 31) / 32);
+  k_rows_of<<<(unsigned)(tiles < 152 * 8 ? tiles : 152 * 8), 256, 0, st>>>(src, ld, bound, live, cols, dst, np);
+  ++*launches;
+}
+
+// out[c * ldo + e] = rows[perm[e] * rs + c], 32 sorted positions per tile, 64 columns at a time.
+__global__ void __launch_bounds__(256) k_rows_gather(const double* rows, int64_t rs, const int32_t* perm, int64_t M,
+                                                     int cols, double* out, int64_t ldo) {
+  __shared__ double tile[32][65];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t tiles = (M + 31) >> 5;
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int64_t e0 = t * 32;
+    for (int cc = 0; cc < cols; cc += 64) {
+      for (int r = warp; r < 32; r += 8) {
+        const int64_t e = e0 + r;
+        if (e < M) {
+          const double* src = rows + (int64_t)perm[e] * rs + cc;
+          tile[r][lane] = cc + lane < cols ? src[lane] : 0.0;
+          tile[r][lane + 32] = cc + 32 + lane < cols ? src[lane + 32] : 0.0;
+        }
+      }
+      __syncthreads();
+      const int64_t e = e0 + lane;
+      for (int c = cc + warp; c < cc + 64 && c < cols; c += 8)
+        if (e < M) out[(int64_t)c * ldo + e] = tile[lane][c - cc];
+      __syncthreads();
+    }
+  }
+}
+
+void rows_gather(const double* rows, int64_t rs, const int32_t* perm, int64_t M, int cols, double* out,
+                 int64_t ldo, cudaStream_t st, int64_t* launches) {
+  if (cols <= 0 || M <= 0) return;
+  const int64_t tiles = (M + 31) / 32;
+  k_rows_gather<<<(unsigned)(tiles < 152 * 8 ? tiles : 152 * 8), 256, 0, st>>>(rows, rs, perm, M, cols, out, ldo);
+  ++*launches;
+}
+
 // ------------------------------------------------------------------ relations (v = 1)
 struct LeafRow {
   int32_t src;   // input row
@@ -189,7 +263,7 @@ __global__ void __launch_bounds__(256) k_leaf_agg(LeafParams p) {
     for (int i = 0; i < kHtItems; ++i) rw[i] = leaf_row(p, e0 + i);
     for (int c = 0; c < p.N; ++c) {
       double xs[kHtItems];
-      load_leaf_items(p, rw, e0, c, false, xs);
+      load_leaf_items(p, rw, e0, c, p.sorted_ready != 0, xs);
       int f = 0;
       double s = 0.0;
 #pragma unroll
@@ -283,7 +357,7 @@ __global__ void __launch_bounds__(256) k_leaf_agg_mx(LeafParams p) {
     for (int i = 0; i < kHtItems; ++i) rw[i] = leaf_row(p, e0 + i);
     for (int c = 0; c < p.N; ++c) {
       double xs[kHtItems];
-      load_leaf_items(p, rw, e0, c, false, xs);
+      load_leaf_items(p, rw, e0, c, p.sorted_ready != 0, xs);
       int f = 0;
       dfl s{0.0f, 0.0f};
 #pragma unroll
@@ -418,19 +492,63 @@ __device__ __forceinline__ GenRow gen_row(const GenParams& p, int64_t e, int64_t
   return r;
 }
 
-// Data[x_i : column] of process_and_join_children (Alg. 4): own heads times prod_j s_j, or
-// the child's generalized heads (looked up at x_ij) times sqrt(rows) prod_{j' != j} s_j'.
-__device__ __forceinline__ double join_value(const GenParams& p, int32_t g, int2 d) {
+// Data[x_i : column] of process_and_join_children (Alg. 4) for every group, column-major
+// (J[c * ldj + g]): the own heads times prod_j s_j, or the child's passed-up row (looked up
+// at x_ij) times sqrt(rows) prod_{j' != j} s_j' (factors in fac; 0 where x_ij is missing).
+// The own heads go with lanes over groups (coalesced); the children's rows are read whole
+// from their row-major copies (lanes over columns) into a shared tile and written as column
+// segments of 32 groups.
+__global__ void __launch_bounds__(256) k_gen_gather(GenParams p, double* J, int64_t ldj) {
+  __shared__ double tile[32][33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nf = 1 + p.n_child;
-  double src;
-  if (d.x == 0) {
-    src = p.heads[(int64_t)d.y * p.ldh + g];
-  } else {
-    const int32_t q = p.q[(int64_t)(d.x - 1) * p.M + g];
-    if (q < 0) return 0.0;
-    src = p.cdata[d.x - 1][(int64_t)d.y * p.cld[d.x - 1] + q];
+  const int64_t G = p.sizes[0];
+  const int64_t tiles = (G + 31) >> 5;
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int64_t g0 = t * 32;
+    for (int c = warp; c < p.N; c += 8) {
+      const int2 d = p.coldesc[c];
+      const int64_t g = g0 + lane;
+      if (d.x == 0 && g < G) J[(int64_t)c * ldj + g] = p.heads[(int64_t)d.y * p.ldh + g] * p.fac[g * nf];
+    }
+    for (int cc = 0; cc < p.N; cc += 32) {
+      for (int r = warp; r < 32; r += 8) {
+        const int64_t g = g0 + r;
+        const int c = cc + lane;
+        double v = 0.0;
+        if (g < G && c < p.N) {
+          const int2 d = p.coldesc[c];
+          if (d.x > 0) {
+            const int32_t q = p.q[(int64_t)(d.x - 1) * p.M + g];
+            if (q >= 0) v = p.crow[d.x - 1][(int64_t)q * p.cnp[d.x - 1] + d.y] * p.fac[g * nf + d.x];
+          }
+        }
+        tile[r][lane] = v;
+      }
+      __syncthreads();
+      const int64_t g = g0 + lane;
+      for (int c = cc + warp; c < cc + 32 && c < p.N; c += 8)
+        if (p.coldesc[c].x > 0 && g < G) J[(int64_t)c * ldj + g] = tile[lane][c - cc];
+      __syncthreads();
+    }
   }
-  return src * p.fac[(int64_t)g * nf + d.x];
+}
+
+// kHtItems joined values of column c for one lane's consecutive groups (16-byte loads)
+__device__ __forceinline__ void load_joined(const GenParams& p, const GenRow (&rw)[kHtItems], int64_t e0, int c,
+                                            int64_t G, double (&Ds)[kHtItems]) {
+  const double* col = p.jdata + (int64_t)c * p.ldj + e0;
+  if (e0 + kHtItems <= G) {
+#pragma unroll
+    for (int i = 0; i < kHtItems; i += 2) {
+      const double2 v = *reinterpret_cast<const double2*>(col + i);
+      Ds[i] = v.x;
+      Ds[i + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < kHtItems; ++i) Ds[i] = rw[i].ok ? col[i] : 0.0;
+  }
 }
 
 __global__ void __launch_bounds__(256) k_gen_agg(GenParams p) {
@@ -445,13 +563,14 @@ __global__ void __launch_bounds__(256) k_gen_agg(GenParams p) {
 #pragma unroll
     for (int i = 0; i < kHtItems; ++i) rw[i] = gen_row(p, e0 + i, G);
     for (int c = 0; c < p.N; ++c) {
-      const int2 d = p.coldesc[c];
+      double Ds[kHtItems];
+      load_joined(p, rw, e0, c, G, Ds);
       int f = 0;
       double s = 0.0;
 #pragma unroll
       for (int i = 0; i < kHtItems; ++i) {
         if (!rw[i].ok) continue;
-        const double x = rw[i].v * join_value(p, rw[i].g, d);
+        const double x = rw[i].v * Ds[i];
         if (rw[i].k == 0) { f = 1; s = x; } else { s += x; }
       }
       const int64_t slot = (int64_t)c * p.n_tiles + t;
@@ -481,14 +600,12 @@ __global__ void __launch_bounds__(256, 2) k_gen_emit(GenParams p) {
       gv[i] = gam * rw[i].v;
     }
     for (int c = 0; c < p.N; ++c) {
-      const int2 d = p.coldesc[c];
       const int64_t slot = (int64_t)c * p.n_tiles + t;
       const int fe = p.lflag[slot * 32 + lane];
       const double se = p.lsum[slot * 32 + lane];
       double run = fe ? se : p.tcarry[slot] + se;
-      double Ds[kHtItems];                 // all loads first: the stores below may alias the sources
-#pragma unroll
-      for (int i = 0; i < kHtItems; ++i) Ds[i] = rw[i].ok ? join_value(p, rw[i].g, d) : 0.0;
+      double Ds[kHtItems];
+      load_joined(p, rw, e0, c, G, Ds);
 #pragma unroll
       for (int i = 0; i < kHtItems; ++i) {
         if (!rw[i].ok) continue;
@@ -502,14 +619,95 @@ __global__ void __launch_bounds__(256, 2) k_gen_emit(GenParams p) {
   }
 }
 
-// Root: Out.append(Data) -- one row per root group over all N columns.
-__global__ void k_root_rows(GenParams p) {
+// ------------------------------------------------------------------ mixed precision (join)
+// The generalized head/tail scans of the mixed path on the FP32 pipe: the weights v, W and
+// gamma of every group and the joined values are split into float pairs (exactly enough,
+// 2^-47), the running sum P of v D and W D - v P are formed in double-float, and each tail
+// is rounded once to float for the float TSQR leaf.  Carries between lanes and tiles stay
+// float64 (one conversion per lane and column); the X_p group sums are stored as a float
+// pair's bits and finished by k_gen_heads_finish.
+__global__ void __launch_bounds__(256) k_gen_agg_mx(GenParams p) {
+  const int lane = threadIdx.x & 31;
   const int64_t G = p.sizes[0];
-  const int64_t total = G * p.N;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = i / G, g = i - c * G;
-    p.rootrows[c * p.M + g] = join_value(p, (int32_t)g, p.coldesc[c]);
+  const int64_t nt = (G + kHtTile - 1) / kHtTile;
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t = wid; t < nt; t += nwarps) {
+    const int64_t e0 = t * kHtTile + (int64_t)lane * kHtItems;
+    GenRow rw[kHtItems];
+    dfl vv[kHtItems];
+#pragma unroll
+    for (int i = 0; i < kHtItems; ++i) {
+      rw[i] = gen_row(p, e0 + i, G);
+      vv[i] = df_from_double(rw[i].v);
+    }
+    for (int c = 0; c < p.N; ++c) {
+      double Ds[kHtItems];
+      load_joined(p, rw, e0, c, G, Ds);
+      int f = 0;
+      dfl s{0.0f, 0.0f};
+#pragma unroll
+      for (int i = 0; i < kHtItems; ++i) {
+        if (!rw[i].ok) continue;
+        const dfl x = df_mul(vv[i], df_from_double(Ds[i]));
+        if (rw[i].k == 0) { f = 1; s = x; } else { s = df_add(s, x); }
+      }
+      pair_scan_incl_df(f, s, lane);
+      int fe = __shfl_up_sync(0xffffffffu, f, 1);
+      float eh = __shfl_up_sync(0xffffffffu, s.hi, 1), el = __shfl_up_sync(0xffffffffu, s.lo, 1);
+      if (lane == 0) { fe = 0; eh = 0.0f; el = 0.0f; }
+      const int64_t slot = (int64_t)c * p.n_tiles + t;
+      p.lflag[slot * 32 + lane] = (uint8_t)fe;
+      p.lsum[slot * 32 + lane] = df_to_double(dfl{eh, el});
+      if (lane == 31) {
+        p.tflag[slot] = (uint8_t)f;
+        p.tsum[slot] = df_to_double(s);
+      }
+    }
+  }
+}
+
+// gtail = gamma (W D - v P), rounded once to float
+__global__ void __launch_bounds__(256, 2) k_gen_emit_mx(GenParams p) {
+  const int lane = threadIdx.x & 31;
+  const int64_t G = p.sizes[0];
+  const int64_t nt = (G + kHtTile - 1) / kHtTile;
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t = wid; t < nt; t += nwarps) {
+    const int64_t e0 = t * kHtTile + (int64_t)lane * kHtItems;
+    GenRow rw[kHtItems];
+    dfl vv[kHtItems], ww[kHtItems];
+    float gam[kHtItems];
+#pragma unroll
+    for (int i = 0; i < kHtItems; ++i) {
+      rw[i] = gen_row(p, e0 + i, G);
+      vv[i] = df_from_double(rw[i].v);
+      ww[i] = rw[i].ok ? df_from_double(p.vw[(int64_t)rw[i].g * 3 + 1]) : dfl{0.0f, 0.0f};
+      gam[i] = rw[i].ok ? df_from_double(p.vw[(int64_t)rw[i].g * 3 + 2]).hi : 0.0f;
+    }
+    for (int c = 0; c < p.N; ++c) {
+      const int64_t slot = (int64_t)c * p.n_tiles + t;
+      const int fe = p.lflag[slot * 32 + lane];
+      const double se = p.lsum[slot * 32 + lane];
+      dfl run = df_from_double(fe ? se : p.tcarry[slot] + se);
+      double Ds[kHtItems];
+      load_joined(p, rw, e0, c, G, Ds);
+      float* tcol = p.gtails32 + (int64_t)c * p.M;
+#pragma unroll
+      for (int i = 0; i < kHtItems; ++i) {
+        if (!rw[i].ok) continue;
+        const dfl D = df_from_double(Ds[i]);
+        if (rw[i].k == 0) run = dfl{0.0f, 0.0f};
+        if (rw[i].k > 0) {
+          const dfl d = df_add(df_mul(ww[i], D), df_neg(df_mul(vv[i], run)));
+          tcol[rw[i].trow] = gam[i] * (d.hi + d.lo);
+        }
+        run = df_add(run, df_mul(vv[i], D));
+        if (rw[i].last)
+          p.data2[(int64_t)c * p.M + rw[i].pg] = __hiloint2double(__float_as_int(run.hi), __float_as_int(run.lo));
+      }
+    }
   }
 }
 
@@ -520,22 +718,32 @@ __global__ void k_gen_heads_finish(GenParams p) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = k / P, q = k - c * P;
-    p.data2[c * p.M + q] *= p.hf[q];
+    double s = p.data2[c * p.M + q];
+    if (p.gtails32) s = (double)__int_as_float(__double2hiint(s)) + (double)__int_as_float(__double2loint(s));
+    p.data2[c * p.M + q] = s * p.hf[q];
   }
 }
 
+static unsigned gather_grid(int64_t rows) {
+  const int64_t tiles = (rows + 31) / 32;
+  return (unsigned)(tiles < 1 ? 1 : (tiles < 152 * 8 ? tiles : 152 * 8));
+}
+
 void gen_heads_tails(const GenParams& p, cudaStream_t st, int64_t* launches) {
-  if (p.is_root) {
-    k_root_rows<<<grid_for(p.M * (int64_t)p.N, 256, 152 * 16), 256, 0, st>>>(p);
+  if (p.is_root) {          // Out.append(Data): the joined Data is the root block itself
+    k_gen_gather<<<gather_grid(p.M), 256, 0, st>>>(p, p.rootrows, p.M);
     ++*launches;
     return;
   }
+  k_gen_gather<<<gather_grid(p.M), 256, 0, st>>>(p, const_cast<double*>(p.jdata), p.ldj);
   const unsigned g = ht_grid(p.n_tiles);
-  k_gen_agg<<<g, 256, 0, st>>>(p);
+  if (p.gtails32) k_gen_agg_mx<<<g, 256, 0, st>>>(p);
+  else k_gen_agg<<<g, 256, 0, st>>>(p);
   k_tile_carry<<<p.N, kCarryThreads, 0, st>>>(p.tflag, p.tsum, p.tcarry, p.n_tiles, p.sizes);
-  k_gen_emit<<<g, 256, 0, st>>>(p);
+  if (p.gtails32) k_gen_emit_mx<<<g, 256, 0, st>>>(p);
+  else k_gen_emit<<<g, 256, 0, st>>>(p);
   k_gen_heads_finish<<<grid_for(p.M * (int64_t)p.N, 256, 152 * 8), 256, 0, st>>>(p);
-  *launches += 4;
+  *launches += 5;
 }
 
 }  // namespace fig

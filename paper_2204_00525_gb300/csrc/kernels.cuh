@@ -147,6 +147,7 @@ struct LeafParams {
   int64_t ldt;
   float* tails32;            // mixed precision: float tails (leading dimension ldt) instead of tails
   float* tails32lo;          // with tails32, optional: the low parts (tail = tails32 + tails32lo)
+  int sorted_ready;          // 1: sdata already holds the data in sorted order (k_rows_gather)
   double* heads;
   int64_t ldh;
   uint8_t* tflag;
@@ -172,8 +173,13 @@ struct GenParams {
   const int32_t* q;          // [n_child * M]
   const double* cdata[kMaxChildren];
   int64_t cld[kMaxChildren];
+  const double* crow[kMaxChildren];   // row-major copies of cdata (row stride cnp)
+  int cnp[kMaxChildren];
+  const double* jdata;       // the node's joined Data [G x N_sub], ld ldj (k_gen_gather)
+  int64_t ldj;
   const int2* coldesc;
   double* gtails;            // [G - P x N_sub], ld M
+  float* gtails32;           // mixed path (not refined): float generalized tails instead, ld M
   double* data2;             // [P x N_sub], ld M
   double* rootrows;          // root only: [G x N], ld M
   uint8_t* tflag;
@@ -186,6 +192,17 @@ struct GenParams {
 };
 
 void beta_table(double2* beta, int64_t len, cudaStream_t st);
+// Row moves for the gathers: a row-major copy of a column-major table (rows beyond *live,
+// if given, are skipped), and the sorted copy out[c][e] = rows[perm[e]][c].
+void rows_of(const double* src, int64_t ld, int64_t bound, const int32_t* live, int cols, double* dst, int np,
+             cudaStream_t st, int64_t* launches);
+void rows_gather(const double* rows, int64_t rs, const int32_t* perm, int64_t M, int cols, double* out,
+                 int64_t ldo, cudaStream_t st, int64_t* launches);
+inline int row_pitch(int cols) { return (cols + 1) & ~1; }
+// Whole-row gathers move about 4 x 8 N bytes per row (copy in, copy out, gather in, sorted
+// copy out) against N sectors of 32 bytes for the plain gather, part of which hit L2 while
+// the table is not much larger than L2: they pay for tables of 1 GiB and more.
+inline bool row_gather_pays(int64_t rows, int cols) { return cols > 0 && (double)rows * cols * 8.0 >= 1073741824.0; }
 void leaf_heads_tails(const LeafParams& p, const int32_t* sizes, cudaStream_t st, int64_t* launches);
 void gen_heads_tails(const GenParams& p, cudaStream_t st, int64_t* launches);
 
@@ -234,7 +251,7 @@ cudaError_t tsqr_set_attributes();
 size_t jacobi_smem(int N);
 cudaError_t svd_set_attributes();
 void jacobi_svd(const double* R, int64_t ldr, int N, double* W, double* V, double* sigma,
-                double* Vout, int* err, cudaStream_t st, int64_t* launches);
+                double* Vout, int* err, cudaStream_t st, int64_t* launches, int max_sweeps);
 void square_values(const double* s, double* out, int k, cudaStream_t st, int64_t* launches);
 
 // figaro_last_error's message for entry points outside api.cu: record_error sets it and

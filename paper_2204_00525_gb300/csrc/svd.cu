@@ -13,7 +13,7 @@ constexpr int kSvdMaxSweeps = 40;
 
 __global__ void __launch_bounds__(kSvdThreads) k_jacobi(const double* R, int64_t ldr, int N, double* Wg,
                                                         double* Vg, double* sigma, double* Vout, int use_smem,
-                                                        int* err) {
+                                                        int max_sweeps, int* err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int rotations;
   double* W = use_smem ? reinterpret_cast<double*>(smem_raw) : Wg;   // column j at W + j N
@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(kSvdThreads) k_jacobi(const double* R, int64_t
   __syncthreads();
   const int npad = N + (N & 1);
   int sweep = 0;
-  for (; sweep < kSvdMaxSweeps; ++sweep) {
+  for (; sweep < max_sweeps; ++sweep) {
     if (tid == 0) rotations = 0;
     __syncthreads();
     for (int r = 0; r < npad - 1; ++r) {
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(kSvdThreads) k_jacobi(const double* R, int64_t
     __syncthreads();
     if (rot == 0) break;
   }
-  if (sweep == kSvdMaxSweeps && tid == 0) set_error(err, FIGARO_ERR_TIMEOUT);
+  if (sweep == max_sweeps && tid == 0) set_error(err, FIGARO_ERR_TIMEOUT);
   // sigma_j = ||W_j||, kept in the first row of the scratch after the loop
   double* sig = reinterpret_cast<double*>(smem_raw) + (use_smem ? 2 * (int64_t)N * N : 0);
   for (int j = warp; j < N; j += nw) {
@@ -121,11 +121,12 @@ cudaError_t svd_set_attributes() {
 }
 
 void jacobi_svd(const double* R, int64_t ldr, int N, double* W, double* V, double* sigma, double* Vout,
-                int* err, cudaStream_t st, int64_t* launches) {
+                int* err, cudaStream_t st, int64_t* launches, int max_sweeps) {
   size_t smem = jacobi_smem(N);
   const int use_smem = smem <= 200 * 1024;
   if (!use_smem) smem = (size_t)N * sizeof(double);
-  k_jacobi<<<1, kSvdThreads, smem, st>>>(R, ldr, N, W, V, sigma, Vout, use_smem, err);
+  k_jacobi<<<1, kSvdThreads, smem, st>>>(R, ldr, N, W, V, sigma, Vout, use_smem,
+                                        max_sweeps > 0 ? max_sweeps : kSvdMaxSweeps, err);
   ++*launches;
 }
 
@@ -264,7 +265,7 @@ extern "C" int figaro_svd_from_r_static(const double* R, int64_t ldr, int32_t n,
   if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess)
     return record_error(FIGARO_ERR_CUDA, "figaro_svd_from_r_static: clearing the error word failed");
   const size_t smem = (size_t)n * sizeof(double);
-  k_jacobi<<<1, kSvdThreads, smem, st>>>(R, ldr, n, W, Vw, sigma, V, 0, err);
+  k_jacobi<<<1, kSvdThreads, smem, st>>>(R, ldr, n, W, Vw, sigma, V, 0, kSvdMaxSweeps, err);
   cudaError_t le = cudaGetLastError();
   if (le != cudaSuccess)
     return record_error(FIGARO_ERR_CUDA, cudaGetErrorString(le));

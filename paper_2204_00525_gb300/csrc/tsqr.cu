@@ -259,10 +259,11 @@ static void launch_givens(const TsqrBlock& b, cudaStream_t st) {
 // w_j = tau' (T_kj + X[:, k]^T X[:, j] / v0), T_kj -= w_j, X[:, j] -= (w_j / v0) X[:, k].  This is
 // Householder QR of the stacked [T; X] with the zeros of T skipped, 2 m n^2 flops per chunk
 // of m rows, so a block of M rows costs the 2 M n^2 of one tall QR and no tree work inside a
-// thread block.  The leaf gives one triangle per b.seg chunks; tree levels fold b.fan such
-// triangles each, several stacked in one chunk when they fit, skipping the rows that are
-// zero in the column being reduced (row i of an upper triangle is zero before column i),
-// (2/3) n^3 flops per triangle.
+// thread block.  The leaf gives one triangle per b.seg chunks; a tree level reduces b.fan
+// such triangles per unit: T starts as the first and the others are folded in, several
+// stacked in one chunk when they fit, skipping the rows that are zero in the column being
+// reduced (row i of an upper triangle is zero before column i), (2/3) n^3 flops per
+// triangle.
 //
 // Per column k, two passes separated by barriers.  Pass A: warps 0-7 form partial dot
 // products of column k with columns k+1.. over row slices (slice s of S takes rows s,
@@ -775,9 +776,21 @@ __global__ void __launch_bounds__(kFoldThreads, sizeof(E) == 4 ? 2 : 1)
   int64_t units = (live + per - 1) / per;
   if (units < 1) units = 1;                   // an empty block still leaves a (zero) triangle
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-    for (int i = threadIdx.x; i < n * n; i += blockDim.x) T[i] = E(0);
-    __syncthreads();
     const int64_t q1 = (u + 1) * per < live ? (u + 1) * per : live;
+    int64_t qs = u * per;
+    if (level > 0) {
+      // T starts as the unit's first triangle (folding it into a zero T would only
+      // reproduce it), and the others are folded in
+      const double* src = tri_in + qs * n * n;
+      for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+        const int r = i / n, c = i - r * n;
+        T[i] = r <= c ? (E)src[(int64_t)c * n + r] : E(0);
+      }
+      ++qs;
+    } else {
+      for (int i = threadIdx.x; i < n * n; i += blockDim.x) T[i] = E(0);
+    }
+    __syncthreads();
     if (level == 0) {
       for (int64_t q = u * per; q < q1; ++q) {
         const int64_t r0 = q * mc;
@@ -799,7 +812,7 @@ __global__ void __launch_bounds__(kFoldThreads, sizeof(E) == 4 ? 2 : 1)
           fold_chunk<E>(X, ldx, m, 1, n, 0, false, T, tglob, red);
       }
     } else if (stack >= 2) {
-      for (int64_t q = u * per; q < q1; q += stack) {
+      for (int64_t q = qs; q < q1; q += stack) {
         const int cnt = (int)((q1 - q) < stack ? (q1 - q) : stack);
         for (int c = warp; c < n; c += nwarps) {
           E* dst = X + (int64_t)c * ldx;
@@ -812,7 +825,7 @@ __global__ void __launch_bounds__(kFoldThreads, sizeof(E) == 4 ? 2 : 1)
         fold_chunk<E>(X, ldx, n, cnt, n, 0, true, T, tglob, red);
       }
     } else {
-      for (int64_t q = u * per; q < q1; ++q) {
+      for (int64_t q = qs; q < q1; ++q) {
         const double* src = tri_in + q * n * n;
         for (int r0 = 0; r0 < n; r0 += mc) {
           const int m = (n - r0) < mc ? (n - r0) : mc;
@@ -883,6 +896,70 @@ __global__ void k_tsqr_stack(const TsqrBlock* blocks, int nb, int stack_rows, in
   }
 }
 
+// Final QR of the stacked block triangles by folding (n <= 256): the triangle of a block
+// that covers every column (the root's Data) becomes T as it is, and every other block
+// triangle, embedded at its global columns, is folded in as row pieces of an upper triangle:
+// row r of a block triangle is zero before global column cols[r] >= cols[0] + r, so a piece
+// starting at row p is the tri case of fold_chunk with r0 = cols[p].  The stack's zeros are
+// skipped, where the dense stack of S rows would cost 2 S N^2 flops in a leaf and a tree.
+__global__ void __launch_bounds__(kFoldThreads, 1)
+    k_tsqr_stack_fold(const TsqrBlock* blocks, int nb, int N, int mc, int tsm, double* Tglob, double* tri_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* red = reinterpret_cast<double*>(smem_raw);
+  double* X = red + fold_red_elems(N);
+  const int ldx = mc + 1;
+  double* T = tsm ? X + (int64_t)ldx * N : Tglob;
+  const bool tglob = !tsm;
+  int full = -1;
+  for (int bi = 0; bi < nb && full < 0; ++bi) {
+    const TsqrBlock& b = blocks[bi];
+    if (b.n != N || block_rows(b) <= 0) continue;
+    bool ident = true;
+    for (int c = 0; c < N; ++c) ident = ident && b.cols[c] == c;
+    if (ident) full = bi;
+  }
+  const double* tf = full >= 0 ? blocks[full].tri[blocks[full].top] : nullptr;
+  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+    const int r = idx / N, c = idx - r * N;          // T is row-major
+    T[idx] = (tf && r <= c) ? tf[(int64_t)c * N + r] : 0.0;
+  }
+  __syncthreads();
+  for (int bi = 0; bi < nb; ++bi) {
+    const TsqrBlock& b = blocks[bi];
+    if (bi == full || block_rows(b) <= 0) continue;
+    const int n = b.n;
+    const double* tri = b.tri[b.top];               // column-major n x n, upper
+    for (int p = 0; p < n; p += mc) {
+      const int h = (n - p) < mc ? (n - p) : mc;
+      for (int idx = threadIdx.x; idx < ldx * N; idx += blockDim.x) X[idx] = 0.0;
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < h * n; idx += blockDim.x) {
+        const int c = idx / h, i = idx - c * h;     // local column c, piece row i (block row p + i)
+        if (p + i <= c) X[(int64_t)b.cols[c] * ldx + i] = tri[(int64_t)c * n + p + i];
+      }
+      __syncthreads();
+      fold_chunk<double>(X, ldx, h, 1, N, b.cols[p], true, T, tglob, red);
+    }
+  }
+  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+    const int c = idx / N, r = idx - c * N;
+    tri_out[idx] = r <= c ? (tglob ? __ldcg(T + (int64_t)r * N + c) : T[(int64_t)r * N + c]) : 0.0;
+  }
+}
+
+// Shared-memory plan of k_tsqr_stack_fold: rows per piece and whether T fits beside X.
+static void stack_fold_plan(int N, int& mc, int& tsm, size_t& smem) {
+  const size_t red = (size_t)fold_red_elems(N) * sizeof(double);
+  const size_t tbytes = (size_t)N * N * sizeof(double);
+  tsm = tbytes <= kSmemCap / 4 ? 1 : 0;
+  const size_t rest = kSmemCap - red - (tsm ? tbytes : 0);
+  int64_t m = (int64_t)(rest / (sizeof(double) * (size_t)N)) - 1;
+  m = (m / 32) * 32;
+  if (m > 512) m = 512;
+  mc = (int)m;
+  smem = red + (size_t)(mc + 1) * N * sizeof(double) + (tsm ? tbytes : 0);
+}
+
 // R = the stack's triangle with every row multiplied by the sign of its diagonal entry.
 __global__ void k_write_r(const double* tri, int N, double* R, int64_t ldr) {
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N * N; idx += gridDim.x * blockDim.x) {
@@ -936,9 +1013,10 @@ static bool fold_plan(TsqrBlock& b, bool mixed, size_t esz) {
   b.fold_tc = tc;
   b.warp_min = 0;
   b.tile = (int)mc;
-  // tree levels: as many triangles as one chunk stacks (at least 4, at most 16)
+  // tree levels: a unit copies its first triangle and folds the others in, as many per
+  // chunk as one chunk stacks, so one chunk per unit and level: fan = stack + 1 (2..16)
   const int64_t stack = mc / n;
-  b.fan = (int)(stack < 4 ? 4 : (stack > 16 ? 16 : stack));
+  b.fan = (int)(stack + 1 < 2 ? 2 : (stack + 1 > 16 ? 16 : stack + 1));
   const int64_t chunks = (b.bound + mc - 1) / mc;
   const int64_t res = fold_resident(mixed);
   int64_t seg = (chunks + res - 1) / res;
@@ -1041,6 +1119,8 @@ cudaError_t tsqr_set_attributes() {
     e = cudaFuncSetAttribute(k_tsqr_fold<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_tsqr_fold<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tsqr_stack_fold, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
   return e;
 }
 
@@ -1112,6 +1192,16 @@ void tsqr_reduce(TsqrBlock& b, bool mixed, cudaStream_t st, int64_t* launches) {
 void tsqr_final(const TsqrBlock* blocks_dev, int n_blocks, TsqrBlock& stack_blk, double* R, int64_t ldr,
                 cudaStream_t st, int64_t* launches) {
   const int N = stack_blk.n;
+  if (N <= kFoldWorkers) {
+    int mc = 0, tsm = 0;
+    size_t smem = 0;
+    stack_fold_plan(N, mc, tsm, smem);
+    k_tsqr_stack_fold<<<1, kFoldThreads, smem, st>>>(blocks_dev, n_blocks, N, mc, tsm, stack_blk.tri[1],
+                                                     stack_blk.tri[0]);
+    k_write_r<<<grid_for((int64_t)N * N, 256, 64), 256, 0, st>>>(stack_blk.tri[0], N, R, ldr);
+    *launches += 2;
+    return;
+  }
   k_tsqr_stack<<<1, 256, 0, st>>>(blocks_dev, n_blocks, (int)stack_blk.M, N, const_cast<double*>(stack_blk.ptr));
   ++*launches;
   tsqr_leaf(stack_blk, false, st, launches);
