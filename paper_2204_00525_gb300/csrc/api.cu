@@ -553,7 +553,7 @@ static void make_blocks(figaro_plan_s& P) {
       t.kind = BLK_TAILS;
       t.M = n.M;
       t.bound = n.M;
-      tsqr_plan_block(t, mixed, P.opt.leaf == FIGARO_LEAF_GIVENS);
+      tsqr_plan_block(t, mixed, P.opt.leaf == FIGARO_LEAF_GIVENS, P.opt.leaf == FIGARO_LEAF_TCGEN05);
       P.blocks.push_back(t);
       P.stack_rows += t.n;
     }
@@ -565,7 +565,7 @@ static void make_blocks(figaro_plan_s& P) {
       t.prio = true;
       t.M = n.M;
       t.bound = n.M;
-      tsqr_plan_block(t, mixed, P.opt.leaf == FIGARO_LEAF_GIVENS);
+      tsqr_plan_block(t, mixed, P.opt.leaf == FIGARO_LEAF_GIVENS, P.opt.leaf == FIGARO_LEAF_TCGEN05);
       P.blocks.push_back(t);
       P.stack_rows += t.n;
     }
@@ -577,7 +577,7 @@ static void make_blocks(figaro_plan_s& P) {
       t.prio = true;
       t.M = n.M;
       t.bound = n.M;
-      tsqr_plan_block(t, mixed, P.opt.leaf == FIGARO_LEAF_GIVENS);
+      tsqr_plan_block(t, mixed, P.opt.leaf == FIGARO_LEAF_GIVENS, P.opt.leaf == FIGARO_LEAF_TCGEN05);
       P.blocks.push_back(t);
       P.stack_rows += t.n;
     }
@@ -594,6 +594,8 @@ static void make_blocks(figaro_plan_s& P) {
 
 // block pointers that depend on the arena
 static void bind_blocks(figaro_plan_s& P) {
+  for (auto& blk : P.blocks) blk.err = P.err_dev;
+  P.stack_blk.err = P.err_dev;
   size_t bi = 0;
   P.block_lo32.assign(P.blocks.size(), nullptr);
   for (auto& n : P.nodes) {
@@ -1084,7 +1086,8 @@ int figaro_plan(const figaro_join_tree* tree, const figaro_options* opt, void* s
   if (opt) P->opt = *opt; else figaro_default_options(&P->opt);
   if ((P->opt.precision != FIGARO_PREC_FP64 && P->opt.precision != FIGARO_PREC_MIXED &&
        P->opt.precision != FIGARO_PREC_MIXED_REFINED) ||
-      (P->opt.leaf != FIGARO_LEAF_HOUSEHOLDER && P->opt.leaf != FIGARO_LEAF_GIVENS)) {
+      (P->opt.leaf != FIGARO_LEAF_HOUSEHOLDER && P->opt.leaf != FIGARO_LEAF_GIVENS &&
+       P->opt.leaf != FIGARO_LEAF_TCGEN05)) {
     delete P;
     return fail(FIGARO_ERR_INVALID_ARG, "precision");
   }

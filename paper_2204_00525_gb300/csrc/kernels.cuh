@@ -235,9 +235,17 @@ struct TsqrBlock {
   int64_t seg;               // fold path: at most this many chunks folded into one leaf triangle
   int64_t fold_g0;           // fold path: thread blocks of the leaf launch
   bool fold_tc;              // fold path, float leaf: panels with tensor-core trailing updates
+  bool fold_tc5;             // fold path, float leaf on tcgen05 (k_tsqr_fold_tc, 128-row chunks)
+  int* err;                  // the plan's device error word (bounded waits report TIMEOUT)
 };
 
-void tsqr_plan_block(TsqrBlock& b, bool mixed, bool givens = false);
+// tsqr_tc.cu: the float leaf on the 5th-generation tensor cores
+size_t fold_tc_smem(int n);
+bool fold_tc_fits(int n);
+void launch_fold_tc(const TsqrBlock& b, double* tri_out, int* err, cudaStream_t st);
+cudaError_t fold_tc_set_attributes();
+
+void tsqr_plan_block(TsqrBlock& b, bool mixed, bool givens = false, bool tcgen05 = false);
 int64_t tsqr_tri_elems(const TsqrBlock& b);
 int64_t tsqr_scratch_elems(const TsqrBlock& b, bool mixed);
 void tsqr_leaf(const TsqrBlock& b, bool mixed, cudaStream_t st, int64_t* launches);

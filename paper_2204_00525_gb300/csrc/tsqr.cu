@@ -995,7 +995,7 @@ static size_t cta_smem(int lda, int n, size_t esz) { return (kRedElems + (size_t
 // triangle in shared memory when it takes at most a quarter of it, else in a global slot
 // per thread block), one leaf triangle per resident thread block (at most 16 chunks each on
 // the float path, whose error grows with the number of folds into one triangle).
-static bool fold_plan(TsqrBlock& b, bool mixed, size_t esz) {
+static bool fold_plan(TsqrBlock& b, bool mixed, size_t esz, bool tcgen05) {
   const int n = b.n;
   if (n > kFoldWorkers) return false;          // T rows are staged one element per worker thread
   const size_t budget = fold_budget(mixed);
@@ -1013,12 +1013,21 @@ static bool fold_plan(TsqrBlock& b, bool mixed, size_t esz) {
   b.fold_tc = tc;
   b.warp_min = 0;
   b.tile = (int)mc;
+  // on request (options.leaf = FIGARO_LEAF_TCGEN05), the float leaf on tcgen05 where its
+  // shared-memory layout fits: 128-row chunks (the tree levels fold with the same chunk
+  // height), one thread block per SM
+  b.fold_tc5 = tcgen05 && mixed && fold_tc_fits(n);
+  if (b.fold_tc5) {
+    b.fold_tc = false;
+    b.tile = 128;
+    mc = 128;
+  }
   // tree levels: a unit copies its first triangle and folds the others in, as many per
   // chunk as one chunk stacks, so one chunk per unit and level: fan = stack + 1 (2..16)
   const int64_t stack = mc / n;
   b.fan = (int)(stack + 1 < 2 ? 2 : (stack + 1 > 16 ? 16 : stack + 1));
   const int64_t chunks = (b.bound + mc - 1) / mc;
-  const int64_t res = fold_resident(mixed);
+  const int64_t res = b.fold_tc5 ? 152 : fold_resident(mixed);
   int64_t seg = (chunks + res - 1) / res;
   if (mixed && seg > 16) seg = 16;
   b.seg = seg < 1 ? 1 : seg;
@@ -1034,7 +1043,7 @@ static bool fold_plan(TsqrBlock& b, bool mixed, size_t esz) {
   return true;
 }
 
-void tsqr_plan_block(TsqrBlock& b, bool mixed, bool givens) {
+void tsqr_plan_block(TsqrBlock& b, bool mixed, bool givens, bool tcgen05) {
   const int n = b.n;
   const size_t esz = mixed ? sizeof(float) : sizeof(double);
   b.nreg = reg_class(n);
@@ -1049,7 +1058,7 @@ void tsqr_plan_block(TsqrBlock& b, bool mixed, bool givens) {
     // their trees with the block-per-tile kernel only, six triangles at a time
     b.fan = b.nreg <= 16 ? b.tile / n : 6;
     if (b.givens) b.tile = kGivensRows;       // leaf chunks of the Givens leaf
-  } else if (fold_plan(b, mixed, esz)) {
+  } else if (fold_plan(b, mixed, esz, tcgen05)) {
     return;
   } else {
     b.warp_min = 0;
@@ -1121,6 +1130,7 @@ cudaError_t tsqr_set_attributes() {
     e = cudaFuncSetAttribute(k_tsqr_fold<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_tsqr_stack_fold, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+  if (e == cudaSuccess) e = fold_tc_set_attributes();
   return e;
 }
 
@@ -1137,7 +1147,8 @@ void tsqr_leaf(const TsqrBlock& b, bool mixed, cudaStream_t st, int64_t* launche
     return;
   }
   if (b.fold) {
-    if (mixed) launch_fold<float>(b, nullptr, b.tri[0], 0, true, st);
+    if (mixed && b.fold_tc5) launch_fold_tc(b, b.tri[0], b.err, st);
+    else if (mixed) launch_fold<float>(b, nullptr, b.tri[0], 0, true, st);
     else launch_fold<double>(b, nullptr, b.tri[0], 0, false, st);
   } else if (b.nreg) {
     if (mixed) {

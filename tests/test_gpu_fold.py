@@ -87,3 +87,17 @@ def test_mixed(case):
     p.close()
     assert np.all(np.isfinite(R)), name
     assert rel_err(R.T @ R, G) < TOL_MIXED, name
+
+
+def test_mixed_tcgen05_leaf(case):
+    """The float leaf on the 5th-generation tensor cores (options.leaf = FIGARO_LEAF_TCGEN05,
+    blocks of 33-112 columns): same R^T R bound as the default float leaf."""
+    from paper_2204_00525_gb300 import binding
+    name, db, G, _ = case
+    p = binding.plan_from_db(db, precision=binding.FIGARO_PREC_MIXED, leaf=binding.FIGARO_LEAF_TCGEN05)
+    R = p.qr_r().cpu().numpy()
+    R2 = p.qr_r().cpu().numpy()
+    p.close()
+    assert np.all(np.isfinite(R)), name
+    assert np.array_equal(R, R2), name                 # deterministic across calls
+    assert rel_err(R.T @ R, G) < TOL_MIXED, name
