@@ -56,7 +56,7 @@ enum figaro_status {
 enum { FIGARO_KEY_I64 = 0, FIGARO_KEY_I32 = 1 };
 enum { FIGARO_COL_MAJOR = 0, FIGARO_ROW_MAJOR = 1 };
 enum { FIGARO_PREC_FP64 = 0, FIGARO_PREC_MIXED = 1, FIGARO_PREC_MIXED_REFINED = 2 };
-enum { FIGARO_LEAF_HOUSEHOLDER = 0, FIGARO_LEAF_GIVENS = 1, FIGARO_LEAF_TCGEN05 = 2 };
+enum { FIGARO_LEAF_HOUSEHOLDER = 0, FIGARO_LEAF_GIVENS = 1, FIGARO_LEAF_TCGEN05 = 2, FIGARO_LEAF_MMA_SYNC = 3 };
 enum { FIGARO_MEM_DEVICE = 0, FIGARO_MEM_HOST = 1 };
 
 /* One relation S_i (§2 "Relations and Joins").
@@ -114,17 +114,18 @@ typedef struct figaro_join_tree {
  *   mem              FIGARO_MEM_DEVICE or FIGARO_MEM_HOST (see the conventions).
  *   stage_timing     1: time every stage with CUDA events (figaro_stage_times).
  *   gradients        1: also hold the workspace of figaro_backward (device memory only).
- *   leaf             FIGARO_LEAF_HOUSEHOLDER (default) or FIGARO_LEAF_GIVENS: TSQR leaves
- *                    of blocks with <= 16 columns by per-thread Givens rotations on
- *                    32-row chunks, skipping exact zeros (the paper's THIN flavour, for
- *                    very sparse blocks; wider blocks keep Householder), in float64 on
- *                    both precisions.  FIGARO_LEAF_TCGEN05: on mixed plans, the float
- *                    leaf of blocks with 33-112 columns on the 5th-generation tensor
- *                    cores (k_tsqr_fold_tc: 128-row chunks, 16-column panels in registers,
- *                    both compact-WY products by tcgen05.mma on bf16 triples with f32
- *                    accumulation in tensor memory); other blocks and FP64 plans as with
- *                    FIGARO_LEAF_HOUSEHOLDER.  Same accuracy class as the default float
- *                    leaf; slower than it on this build (see the design notes).
+ *   leaf             FIGARO_LEAF_HOUSEHOLDER (default): Householder TSQR leaves; on
+ *                    mixed plans the float leaf of blocks with 33-112 columns runs on the
+ *                    5th-generation tensor cores (128-row chunks, 16-column panels in
+ *                    registers, both compact-WY products by tcgen05.mma on bf16 triples
+ *                    with f32 accumulation in tensor memory).  FIGARO_LEAF_TCGEN05: the
+ *                    same, named explicitly.  FIGARO_LEAF_MMA_SYNC: mixed plans fold their
+ *                    33-256-column blocks with split-tf32 mma.sync panel updates instead
+ *                    (the earlier float leaf; same accuracy class, slower).
+ *                    FIGARO_LEAF_GIVENS: TSQR leaves of blocks with <= 16 columns by
+ *                    per-thread Givens rotations on 32-row chunks, skipping exact zeros
+ *                    (the paper's THIN flavour, for very sparse blocks; wider blocks as
+ *                    the default), in float64 on both precisions.
  *   workspace_limit_mib  0 (default): no limit; otherwise figaro_plan fails with
  *                    FIGARO_ERR_NOMEM, allocating nothing, when the plan's device workspace
  *                    would exceed this many MiB (a memory budget for callers that share

@@ -21,7 +21,7 @@ FIGARO_KEY_I64, FIGARO_KEY_I32 = 0, 1
 FIGARO_COL_MAJOR, FIGARO_ROW_MAJOR = 0, 1
 FIGARO_PREC_FP64, FIGARO_PREC_MIXED, FIGARO_PREC_MIXED_REFINED = 0, 1, 2
 FIGARO_PROJ_X, FIGARO_PROJ_Q, FIGARO_PROJ_U, FIGARO_PROJ_SCORES = 0, 1, 2, 3
-FIGARO_LEAF_HOUSEHOLDER, FIGARO_LEAF_GIVENS, FIGARO_LEAF_TCGEN05 = 0, 1, 2
+FIGARO_LEAF_HOUSEHOLDER, FIGARO_LEAF_GIVENS, FIGARO_LEAF_TCGEN05, FIGARO_LEAF_MMA_SYNC = 0, 1, 2, 3
 FIGARO_MEM_DEVICE, FIGARO_MEM_HOST = 0, 1
 DBG = {"sizes": 0, "perm": 1, "group_off": 2, "counts": 3, "pcounts": 4, "tails": 5, "heads": 6,
        "gen_tails": 7, "data": 8, "root_rows": 9}

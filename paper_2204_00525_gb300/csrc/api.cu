@@ -553,7 +553,7 @@ static void make_blocks(figaro_plan_s& P) {
       t.kind = BLK_TAILS;
       t.M = n.M;
       t.bound = n.M;
-      tsqr_plan_block(t, mixed, P.opt.leaf == FIGARO_LEAF_GIVENS, P.opt.leaf == FIGARO_LEAF_TCGEN05);
+      tsqr_plan_block(t, mixed, P.opt.leaf == FIGARO_LEAF_GIVENS, P.opt.leaf != FIGARO_LEAF_MMA_SYNC);
       P.blocks.push_back(t);
       P.stack_rows += t.n;
     }
@@ -565,7 +565,7 @@ static void make_blocks(figaro_plan_s& P) {
       t.prio = true;
       t.M = n.M;
       t.bound = n.M;
-      tsqr_plan_block(t, mixed, P.opt.leaf == FIGARO_LEAF_GIVENS, P.opt.leaf == FIGARO_LEAF_TCGEN05);
+      tsqr_plan_block(t, mixed, P.opt.leaf == FIGARO_LEAF_GIVENS, P.opt.leaf != FIGARO_LEAF_MMA_SYNC);
       P.blocks.push_back(t);
       P.stack_rows += t.n;
     }
@@ -577,7 +577,7 @@ static void make_blocks(figaro_plan_s& P) {
       t.prio = true;
       t.M = n.M;
       t.bound = n.M;
-      tsqr_plan_block(t, mixed, P.opt.leaf == FIGARO_LEAF_GIVENS, P.opt.leaf == FIGARO_LEAF_TCGEN05);
+      tsqr_plan_block(t, mixed, P.opt.leaf == FIGARO_LEAF_GIVENS, P.opt.leaf != FIGARO_LEAF_MMA_SYNC);
       P.blocks.push_back(t);
       P.stack_rows += t.n;
     }
@@ -1087,7 +1087,7 @@ int figaro_plan(const figaro_join_tree* tree, const figaro_options* opt, void* s
   if ((P->opt.precision != FIGARO_PREC_FP64 && P->opt.precision != FIGARO_PREC_MIXED &&
        P->opt.precision != FIGARO_PREC_MIXED_REFINED) ||
       (P->opt.leaf != FIGARO_LEAF_HOUSEHOLDER && P->opt.leaf != FIGARO_LEAF_GIVENS &&
-       P->opt.leaf != FIGARO_LEAF_TCGEN05)) {
+       P->opt.leaf != FIGARO_LEAF_TCGEN05 && P->opt.leaf != FIGARO_LEAF_MMA_SYNC)) {
     delete P;
     return fail(FIGARO_ERR_INVALID_ARG, "precision");
   }

@@ -1013,9 +1013,9 @@ static bool fold_plan(TsqrBlock& b, bool mixed, size_t esz, bool tcgen05) {
   b.fold_tc = tc;
   b.warp_min = 0;
   b.tile = (int)mc;
-  // on request (options.leaf = FIGARO_LEAF_TCGEN05), the float leaf on tcgen05 where its
-  // shared-memory layout fits: 128-row chunks (the tree levels fold with the same chunk
-  // height), one thread block per SM
+  // the float leaf on tcgen05 where its shared-memory layout fits (unless the mma.sync
+  // fold was asked for): 128-row chunks (the tree levels fold with the same chunk height),
+  // one thread block per SM
   b.fold_tc5 = tcgen05 && mixed && fold_tc_fits(n);
   if (b.fold_tc5) {
     b.fold_tc = false;

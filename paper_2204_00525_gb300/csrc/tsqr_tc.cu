@@ -98,6 +98,51 @@ __device__ __forceinline__ void x_put(unsigned char* sm, int col, int row, float
   put_bf(sm, o + 2 * kXSplit, c);
 }
 
+// Two consecutive rows (2r, 2r + 1) of one column share a 32-bit word of every part.
+__device__ __forceinline__ float2 x_get2(const unsigned char* sm, int col, int row_even) {
+  const uint32_t o = kOffX + x_off(col, row_even);
+  const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(sm + o));
+  const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(sm + o + kXSplit));
+  const float2 c = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(sm + o + 2 * kXSplit));
+  return make_float2(a.x + (b.x + c.x), a.y + (b.y + c.y));
+}
+__device__ __forceinline__ void split3x2(float2 x, __nv_bfloat162& a, __nv_bfloat162& b, __nv_bfloat162& c) {
+  a = __float22bfloat162_rn(x);
+  const float2 fa = __bfloat1622float2(a);
+  const float2 r1 = make_float2(x.x - fa.x, x.y - fa.y);
+  b = __float22bfloat162_rn(r1);
+  const float2 fb = __bfloat1622float2(b);
+  c = __float22bfloat162_rn(make_float2(r1.x - fb.x, r1.y - fb.y));
+}
+__device__ __forceinline__ void x_put2(unsigned char* sm, int col, int row_even, float2 x) {
+  __nv_bfloat162 a, b, c;
+  split3x2(x, a, b, c);
+  const uint32_t o = kOffX + x_off(col, row_even);
+  *reinterpret_cast<__nv_bfloat162*>(sm + o) = a;
+  *reinterpret_cast<__nv_bfloat162*>(sm + o + kXSplit) = b;
+  *reinterpret_cast<__nv_bfloat162*>(sm + o + 2 * kXSplit) = c;
+}
+
+// Sixteen consecutive K values of one operand row (3 parts, 16-byte stores): the row's K
+// values 0-7 are 16 contiguous bytes, 8-15 the next core matrix (kVLbo further).
+__device__ __forceinline__ void put_row16(unsigned char* base, uint32_t off, const float (&w)[16]) {
+  uint32_t p[3][8];
+#pragma unroll
+  for (int q = 0; q < 16; q += 2) {
+    __nv_bfloat162 a, b, c;
+    split3x2(make_float2(w[q], w[q + 1]), a, b, c);
+    p[0][q / 2] = *reinterpret_cast<uint32_t*>(&a);
+    p[1][q / 2] = *reinterpret_cast<uint32_t*>(&b);
+    p[2][q / 2] = *reinterpret_cast<uint32_t*>(&c);
+  }
+#pragma unroll
+  for (int part = 0; part < 3; ++part) {
+    *reinterpret_cast<uint4*>(base + off + part * kVSplit) = make_uint4(p[part][0], p[part][1], p[part][2], p[part][3]);
+    *reinterpret_cast<uint4*>(base + off + part * kVSplit + kVLbo) =
+        make_uint4(p[part][4], p[part][5], p[part][6], p[part][7]);
+  }
+}
+
 // Sum over the warp of sixteen values per lane: lane l (l even) returns the total of value
 // ((l >> 4) & 1) * 8 + ((l >> 3) & 1) * 4 + ((l >> 2) & 1) * 2 + ((l >> 1) & 1) (recursive
 // halving: each exchange sends the half the partner keeps).
@@ -155,10 +200,12 @@ __device__ void tc_panel(unsigned char* sm, float* T, int n, int p0, int b) {
 #pragma unroll
     for (int j = 0; j < kTcB; ++j)
       if (j == k) xk = x[j];
+    // every product is formed; only value 0 (the sum of squares) and the dots with the
+    // later panel columns (j > k, j < b) are read below
     float v[kTcB];
     v[0] = xk * xk;
 #pragma unroll
-    for (int j = 1; j < kTcB; ++j) v[j] = (j > k && j < b) ? xk * x[j] : 0.f;
+    for (int j = 1; j < kTcB; ++j) v[j] = xk * x[j];
     const float s = warp_sum16(v, lane);
     if ((lane & 1) == 0) red[(buf * 4 + warp) * 16 + sum16_index(lane)] = s;
     bar_panel();
@@ -188,10 +235,8 @@ __device__ void tc_panel(unsigned char* sm, float* T, int n, int p0, int b) {
     if (lane == k) tpend = beta;
     const float xs = rv * xk;
 #pragma unroll
-    for (int j = 0; j < kTcB; ++j) {
-      const float wj = __shfl_sync(0xffffffffu, wl, j);
-      if (j > k && j < b) x[j] = fmaf(-wj, xs, x[j]);   // x_j -= w'_j x_k / v0
-    }
+    for (int j = 0; j < kTcB; ++j)                      // x_j -= w'_j x_k / v0 (w' = 0 off k < j < b)
+      x[j] = fmaf(-__shfl_sync(0xffffffffu, wl, j), xs, x[j]);
     if (t == 0) {
       tau[k] = taup;
       rvs[k] = rv;
@@ -201,45 +246,37 @@ __device__ void tc_panel(unsigned char* sm, float* T, int n, int p0, int b) {
   bar_panel();                                        // every thread has read T's last row
   if (warp == 0 && lane == b - 1) T[(p0 + b - 1) * n + p0 + lane] = tpend;
   // reflector columns: back into X, and row-major (row t) as the update's A operand
-  unsigned char* A = sm + kOffA;
 #pragma unroll
   for (int q = 0; q < kTcB; ++q) {
-    __nv_bfloat16 a, bb, c;
-    split3(q < b ? x[q] : 0.f, a, bb, c);
-    if (q < b) {
-      const uint32_t o = kOffX + x_off(p0 + q, t);
-      put_bf(sm, o, a);
-      put_bf(sm, o + kXSplit, bb);
-      put_bf(sm, o + 2 * kXSplit, c);
-    }
-    const uint32_t o = v_off(t, q);
-    put_bf(A, o, a);
-    put_bf(A, o + kVSplit, bb);
-    put_bf(A, o + 2 * kVSplit, c);
+    if (q >= b) x[q] = 0.f;
+    if (q < b) x_put(sm, p0 + q, t, x[q]);
   }
+  put_row16(sm + kOffA, v_off(t, 0), x);
 }
 
-// Tw of the panel (warp 0): Tw_qq = tau'_q, Tw[0:q, q] = -tau'_q Tw[0:q, 0:q] z with
-// z_r = y_r^T y_q = (x_r^T x_q) / (v0_r v0_q), the Gram entries read from P.
-__device__ void tc_tw(unsigned char* sm, int p0, int b) {
-  const int lane = threadIdx.x & 31;
-  const float* Ps = reinterpret_cast<const float*>(sm + kOffPs);
-  const float* tau = reinterpret_cast<const float*>(sm + kOffTau);
-  const float* rvs = reinterpret_cast<const float*>(sm + kOffRv);
-  float* Tw = reinterpret_cast<float*>(sm + kOffTw);
-  for (int q = 0; q < b; ++q) {
-    const float tq = tau[q], rq = rvs[q];
-    float val = 0.f;
-    if (lane < q) {
-      float acc = 0.f;
-      for (int s2 = lane; s2 < q; ++s2) acc = fmaf(Tw[lane * kTcB + s2], Ps[(p0 + q) * kPsLd + s2] * rvs[s2] * rq, acc);
-      val = -tq * acc;
-    } else if (lane == q) {
-      val = tq;
+// X[:, p0 + 16 ch + e] -= D2[:, 16 ch + e] for the chunks ch in [ch0, ch1) and columns
+// below c (the pending update, TMEM columns 16 ..), on the 32 rows of sub-partition `sub`
+// (a warp reads only its sub-partition's lanes).  Lanes 2r and 2r + 1 hold rows 2r and
+// 2r + 1: the even lane updates the even columns of both rows, the odd lane the odd ones
+// (one 32-bit word per part).
+__device__ __forceinline__ void tc_apply(unsigned char* sm, uint32_t tmem, int sub, int lane, int p0, int ch0,
+                                         int ch1, int c) {
+  const bool odd = lane & 1;
+  const int row0 = (32 * sub + lane) & ~1;
+  for (int ch = ch0; ch < ch1; ++ch) {
+    float v[16];
+    tc::ld16(tmem + ((uint32_t)(32 * sub) << 16) + 16 + 16 * ch, v);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const float other = __shfl_xor_sync(0xffffffffu, v[e], 1);
+      const int jj = 16 * ch + e;
+      if (((e & 1) != 0) == odd && jj < c) {
+        const int col = p0 + jj;
+        const float2 d = odd ? make_float2(other, v[e]) : make_float2(v[e], other);
+        const float2 xv = x_get2(sm, col, row0);
+        x_put2(sm, col, row0, make_float2(xv.x - d.x, xv.y - d.y));
+      }
     }
-    __syncwarp();
-    if (lane <= q) Tw[lane * kTcB + q] = val;
-    __syncwarp();
   }
 }
 
@@ -287,27 +324,43 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tsqr_fold_tc(TsqrBlock b, dou
       const int64_t r0 = q * kTcRows;
       const int m = (int)((rows - r0) < kTcRows ? (rows - r0) : kTcRows);
       __syncthreads();
-      for (int base_idx = 0; base_idx < kTcWin * kTcRows; base_idx += kTcThreads * 16) {
-        float v[16];                                    // sixteen loads in flight, then the stores
+      constexpr int kPairs = kTcWin * kTcRows / 2;     // (column, row pair)
+      for (int base_idx = 0; base_idx < kPairs; base_idx += kTcThreads * 8) {
+        float2 v[8];                                    // sixteen loads in flight, then the stores
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
+        for (int e = 0; e < 8; ++e) {
           const int idx = base_idx + e * kTcThreads + t;
-          const int c = idx / kTcRows, i = idx - c * kTcRows;
-          v[e] = 0.f;
-          if (c < n && i < m)
-            v[e] = b.ptr32 ? b.ptr32[(int64_t)c * b.ld + r0 + i] : (float)b.ptr[(int64_t)c * b.ld + r0 + i];
+          const int c = idx / (kTcRows / 2), i = 2 * (idx - c * (kTcRows / 2));
+          v[e] = make_float2(0.f, 0.f);
+          if (c < n) {
+            const int64_t g = (int64_t)c * b.ld + r0 + i;
+            if (i < m) v[e].x = b.ptr32 ? b.ptr32[g] : (float)b.ptr[g];
+            if (i + 1 < m) v[e].y = b.ptr32 ? b.ptr32[g + 1] : (float)b.ptr[g + 1];
+          }
         }
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
+        for (int e = 0; e < 8; ++e) {
           const int idx = base_idx + e * kTcThreads + t;
-          x_put(sm, idx / kTcRows, idx % kTcRows, v[e]);
+          const int c = idx / (kTcRows / 2);
+          x_put2(sm, c, 2 * (idx - c * (kTcRows / 2)), v[e]);
         }
       }
       __syncthreads();
+      int cprev = 0;                                    // columns of the pending update in D2
       for (int p0 = 0; p0 < n; p0 += kTcB) {
         const int bw = (n - p0) < kTcB ? (n - p0) : kTcB;
         const int c = n - p0 - bw;                      // trailing columns
-        if (warp < 4) tc_panel(sm, T, n, p0, bw);
+        // The previous panel's update X[:, p0 ..] -= D2 is applied with look-ahead: warps
+        // 0-3 first take its first 16 columns (this panel: each warp its own 32 rows, so a
+        // warp only waits for itself), then factor the panel while warps 4-7 apply the rest.
+        if (warp < 4) {
+          if (cprev > 0) tc_apply(sm, tmem, warp, lane, p0, 0, 1, cprev);
+          __syncwarp();
+          tc_panel(sm, T, n, p0, bw);
+        } else if (cprev > 16) {
+          tc_apply(sm, tmem, warp - 4, lane, p0, 1, (cprev + 15) / 16, cprev);
+        }
+        cprev = 0;
         if (c <= 0) {
           __syncthreads();
           break;
@@ -318,13 +371,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tsqr_fold_tc(TsqrBlock b, dou
         // ---- P = X^T X_v: 128 x 16, K = 128 rows in 8 steps of 16, six products each
         if (t == 0) {
           tc::fence_after_sync();
+          const uint64_t ad0 = tc::desc(base + kOffX, kXLbo, kXSbo);
+          const uint64_t bd0 = tc::desc(base + kOffX + (p0 >> 3) * kXSbo, kXLbo, kXSbo);
           for (int kk = 0; kk < kTcRows / 16; ++kk)
-            for (int pr = 0; pr < 6; ++pr) {
-              const uint64_t ad = tc::desc(base + kOffX + pa[pr] * kXSplit + kk * 2 * kXLbo, kXLbo, kXSbo);
-              const uint64_t bd =
-                  tc::desc(base + kOffX + pb[pr] * kXSplit + (p0 >> 3) * kXSbo + kk * 2 * kXLbo, kXLbo, kXSbo);
-              tc::mma_bf16(tmem, ad, bd, id_p, (kk | pr) != 0);
-            }
+            for (int pr = 0; pr < 6; ++pr)            // the address field (bits 0-13, 16-byte units) advances
+              tc::mma_bf16(tmem, ad0 + ((pa[pr] * kXSplit + kk * 2 * kXLbo) >> 4),
+                           bd0 + ((pb[pr] * kXSplit + kk * 2 * kXLbo) >> 4), id_p, (kk | pr) != 0);
           tc::commit(mbar);
         }
         in_flight = true;
@@ -347,26 +399,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tsqr_fold_tc(TsqrBlock b, dou
         }
         tc::fence_before_sync();
         __syncthreads();
-        if (warp == 0) tc_tw(sm, p0, bw);
+        // G'[r][q] = y_r^T y_q = (x_r^T x_q) / (v0_r v0_q) for r < q: Tw^-1 = diag(1/tau') + G'
+        {
+          const int r = t >> 4, q = t & 15;
+          Tw[t] = (r < q && q < bw) ? Ps[(p0 + q) * kPsLd + r] * rvs[r] * rvs[q] : 0.f;
+        }
         __syncthreads();
-        // ---- W' per trailing column; T's panel rows; W'' = diag(1/v0) W' as the update's B
+        // ---- W' = Tw^T W per trailing column by forward substitution with Tw^-T:
+        // W'_q = tau'_q (W_q - sum_{r<q} G'[r][q] W'_r), W = T[panel rows, j] + diag(1/v0) P[:, j];
+        // T's panel rows -= W'; W'' = diag(1/v0) W' is the update's B operand
         const int cpad = (c + 15) & ~15;
         unsigned char* B2 = sm + kOffB;
+        const float* taus = reinterpret_cast<const float*>(sm + kOffTau);
         for (int jj = t; jj < cpad; jj += kTcThreads) {
           const int j = p0 + bw + jj;
           float w[kTcB];
           if (jj < c) {
 #pragma unroll
-            for (int qq = 0; qq < kTcB; ++qq)
-              w[qq] = qq < bw ? fmaf(rvs[qq], Ps[j * kPsLd + qq], T[(p0 + qq) * n + j]) : 0.f;
+            for (int qq = 0; qq < kTcB; ++qq) {
+              float acc = qq < bw ? fmaf(rvs[qq], Ps[j * kPsLd + qq], T[(p0 + qq) * n + j]) : 0.f;
 #pragma unroll
-            for (int qq = kTcB - 1; qq >= 0; --qq) {    // in place from the last row: w[r], r <= qq, still W
-              if (qq < bw) {
-                float acc = 0.f;
-#pragma unroll
-                for (int r = 0; r <= qq; ++r) acc = fmaf(Tw[r * kTcB + qq], w[r], acc);
-                w[qq] = acc;
-              }
+              for (int r = 0; r < qq; ++r) acc = fmaf(-Tw[r * kTcB + qq], w[r], acc);
+              w[qq] = qq < bw ? taus[qq] * acc : 0.f;
             }
 #pragma unroll
             for (int qq = 0; qq < kTcB; ++qq)
@@ -378,20 +432,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tsqr_fold_tc(TsqrBlock b, dou
 #pragma unroll
             for (int qq = 0; qq < kTcB; ++qq) w[qq] = 0.f;
           }
-#pragma unroll
-          for (int qq = 0; qq < kTcB; ++qq) {
-            __nv_bfloat16 a, bb, cc;
-            split3(w[qq], a, bb, cc);
-            const uint32_t o = v_off(jj, qq);
-            put_bf(B2, o, a);
-            put_bf(B2, o + kVSplit, bb);
-            put_bf(B2, o + 2 * kVSplit, cc);
-          }
+          put_row16(B2, v_off(jj, 0), w);
         }
         tc::fence_proxy_async();
         tc::fence_before_sync();
         __syncthreads();
-        // ---- X_trail -= X_v W'': 128 x cpad, K = 16, six products
+        // ---- X_trail -= X_v W'': 128 x cpad, K = 16, six products, applied by the next panel
         if (t == 0) {
           tc::fence_after_sync();
           const uint32_t id_u = tc::idesc_bf16(128, cpad);
@@ -412,24 +458,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tsqr_fold_tc(TsqrBlock b, dou
         in_flight = false;
         phase ^= 1;
         tc::fence_after_sync();
-        {                                               // epilogue: warp w reads lanes 32 (w % 4)
-          const int sub = warp & 3, half = warp >> 2;
-          const int row = 32 * sub + lane;
-          for (int ch = half; ch < cpad / 16; ch += 2) {
-            float v[16];
-            tc::ld16(tmem + ((uint32_t)(32 * sub) << 16) + 16 + 16 * ch, v);
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-              const int jj = 16 * ch + e;
-              if (jj < c) {
-                const int col = p0 + bw + jj;
-                x_put(sm, col, row, x_get(sm, col, row) - v[e]);
-              }
-            }
-          }
-        }
-        tc::fence_before_sync();
-        __syncthreads();
+        cprev = c;
       }
     }
     if (*abort_flag) break;

@@ -135,12 +135,12 @@ def test_full_size_snowflake():
     print(f"snowflake mixed: R^T R error {err:.3e}, per-column-scaled {serr:.3e}")
     assert err < TOL_MIXED
     assert serr < 10 * TOL_MIXED
-    # the tcgen05 float leaf (the 100-column block; several units per thread block)
-    p = plan_for(db, precision=binding.FIGARO_PREC_MIXED, leaf=binding.FIGARO_LEAF_TCGEN05)
+    # the split-tf32 mma.sync fold instead of the tcgen05 leaf for the 100-column block
+    p = plan_for(db, precision=binding.FIGARO_PREC_MIXED, leaf=binding.FIGARO_LEAF_MMA_SYNC)
     Rt = p.qr_r().cpu().numpy()
     p.close()
     err, serr = rel_err(Rt.T @ Rt, G), scaled_err(Rt.T @ Rt, G)
-    print(f"snowflake mixed, tcgen05 leaf: R^T R error {err:.3e}, per-column-scaled {serr:.3e}")
+    print(f"snowflake mixed, mma.sync fold: R^T R error {err:.3e}, per-column-scaled {serr:.3e}")
     assert err < TOL_MIXED
     assert serr < 10 * TOL_MIXED
 

@@ -13,7 +13,8 @@ root block has n_S + n_T columns and whose tails blocks have n_S and n_T columns
   dup_column   two equal columns (rank deficient: R^T R only)
 
 FP64: R within 1e-10 of the oracle's (relative Frobenius) where R is unique, R^T R within
-1e-10 of A^T A; mixed (float leaf with tensor-core panels): R^T R within 1e-6."""
+1e-10 of A^T A; mixed (the tcgen05 float leaf for 33-112 columns, the split-tf32 mma.sync
+fold for wider blocks or on request): R^T R within 1e-6."""
 import numpy as np
 import pytest
 
@@ -89,12 +90,15 @@ def test_mixed(case):
     assert rel_err(R.T @ R, G) < TOL_MIXED, name
 
 
-def test_mixed_tcgen05_leaf(case):
-    """The float leaf on the 5th-generation tensor cores (options.leaf = FIGARO_LEAF_TCGEN05,
-    blocks of 33-112 columns): same R^T R bound as the default float leaf."""
+@pytest.mark.parametrize("leaf", ["tcgen05", "mma_sync"])
+def test_mixed_leaf_variants(case, leaf):
+    """The float leaf on the 5th-generation tensor cores (the default for blocks of 33-112
+    columns, named explicitly) and the split-tf32 mma.sync fold: same R^T R bound,
+    deterministic across calls."""
     from paper_2204_00525_gb300 import binding
     name, db, G, _ = case
-    p = binding.plan_from_db(db, precision=binding.FIGARO_PREC_MIXED, leaf=binding.FIGARO_LEAF_TCGEN05)
+    lv = binding.FIGARO_LEAF_TCGEN05 if leaf == "tcgen05" else binding.FIGARO_LEAF_MMA_SYNC
+    p = binding.plan_from_db(db, precision=binding.FIGARO_PREC_MIXED, leaf=lv)
     R = p.qr_r().cpu().numpy()
     R2 = p.qr_r().cpu().numpy()
     p.close()
