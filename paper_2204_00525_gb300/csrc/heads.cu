@@ -498,37 +498,66 @@ __device__ __forceinline__ GenRow gen_row(const GenParams& p, int64_t e, int64_t
 // The own heads go with lanes over groups (coalesced); the children's rows are read whole
 // from their row-major copies (lanes over columns) into a shared tile and written as column
 // segments of 32 groups.
+constexpr int kGatherMaxCols = 1024;
+
 __global__ void __launch_bounds__(256) k_gen_gather(GenParams p, double* J, int64_t ldj) {
   __shared__ double tile[32][33];
+  __shared__ int2 cd[kGatherMaxCols];              // column descriptors (N <= 1024)
+  __shared__ int32_t qs[kMaxChildren][32];         // the tile's row of every child's table
+  __shared__ double fs[kMaxChildren + 1][32];      // the tile's join factors
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nf = 1 + p.n_child;
   const int64_t G = p.sizes[0];
   const int64_t tiles = (G + 31) >> 5;
+  for (int c = threadIdx.x; c < p.N; c += blockDim.x) cd[c] = p.coldesc[c];
   for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
     const int64_t g0 = t * 32;
-    for (int c = warp; c < p.N; c += 8) {
-      const int2 d = p.coldesc[c];
-      const int64_t g = g0 + lane;
-      if (d.x == 0 && g < G) J[(int64_t)c * ldj + g] = p.heads[(int64_t)d.y * p.ldh + g] * p.fac[g * nf];
+    __syncthreads();                                 // cd written; the previous tile's reads done
+    for (int idx = threadIdx.x; idx < 32 * nf; idx += blockDim.x) {
+      const int f = idx >> 5, r = idx & 31;
+      const int64_t g = g0 + r;
+      fs[f][r] = g < G ? p.fac[g * nf + f] : 0.0;
+      if (f > 0) qs[f - 1][r] = g < G ? p.q[(int64_t)(f - 1) * p.M + g] : -1;
     }
+    __syncthreads();
+    const int64_t g = g0 + lane;
+    // own heads: lanes over groups, four columns in flight per warp
+    for (int c0 = warp; c0 < p.N; c0 += 32) {
+      double v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = c0 + 8 * u;
+        v[u] = 0.0;
+        if (c < p.N && cd[c].x == 0 && g < G) v[u] = p.heads[(int64_t)cd[c].y * p.ldh + g];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = c0 + 8 * u;
+        if (c < p.N && cd[c].x == 0 && g < G) J[(int64_t)c * ldj + g] = v[u] * fs[0][lane];
+      }
+    }
+    // children's rows: lanes over columns, the warp's four rows loaded before they are used
     for (int cc = 0; cc < p.N; cc += 32) {
-      for (int r = warp; r < 32; r += 8) {
-        const int64_t g = g0 + r;
-        const int c = cc + lane;
-        double v = 0.0;
-        if (g < G && c < p.N) {
-          const int2 d = p.coldesc[c];
-          if (d.x > 0) {
-            const int32_t q = p.q[(int64_t)(d.x - 1) * p.M + g];
-            if (q >= 0) v = p.crow[d.x - 1][(int64_t)q * p.cnp[d.x - 1] + d.y] * p.fac[g * nf + d.x];
-          }
+      const int c = cc + lane;
+      const int2 d = c < p.N ? cd[c] : make_int2(0, 0);
+      double v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = warp + 8 * u;
+        v[u] = 0.0;
+        if (d.x > 0) {
+          const int32_t q = qs[d.x - 1][r];
+          if (q >= 0) v[u] = p.crow[d.x - 1][(int64_t)q * p.cnp[d.x - 1] + d.y];
         }
-        tile[r][lane] = v;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = warp + 8 * u;
+        tile[r][lane] = d.x > 0 ? v[u] * fs[d.x][r] : 0.0;
       }
       __syncthreads();
-      const int64_t g = g0 + lane;
-      for (int c = cc + warp; c < cc + 32 && c < p.N; c += 8)
-        if (p.coldesc[c].x > 0 && g < G) J[(int64_t)c * ldj + g] = tile[lane][c - cc];
+      for (int c2 = cc + warp; c2 < cc + 32 && c2 < p.N; c2 += 8)
+        if (cd[c2].x > 0 && g < G) J[(int64_t)c2 * ldj + g] = tile[lane][c2 - cc];
       __syncthreads();
     }
   }
