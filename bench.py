@@ -51,10 +51,11 @@ PATH3 = ("path3_2m: R1(a;x1..x8) - R2(a,b;y1..y8) - R3(b;z1..z8), 2,000,000 rows
 FP64_PEAK_DERIVED = 152 * 2070e6 * 4 / 1e12   # 152 SMs x 2.07 GHz x 2 DFMA/clk/SM x 2 flop
 REF_SAMPLE = 4                                # the reference arm's rows: the workload's / 4
 GOLDEN_GRAM = os.path.join(ROOT, "tests", "golden", "snowflake_gram.npz")
-# DRAM bytes per input row of the dominant kernel (k_tsqr_fold<double> leaf of the
-# 100-column generalized-tail block), from the ncu capture of the same kernel on a
-# 2M-row snowflake summarised in profiles/tsqr_fold_f64_snowflake.md (scaled by rows).
-DOMINANT_DRAM_BYTES_PER_ROW = None
+# DRAM bytes per row of the dominant kernel (k_tsqr_fold<double>, leaf of the 100-column
+# generalized-tail block): (dram__bytes_read.sum + dram__bytes_write.sum) / rows of the ncu
+# capture of the same kernel on the snowflake with a fifth of the rows, summarised in
+# profiles/tsqr_fold_f64_snowflake.md; the traffic grows with the rows.
+DOMINANT_DRAM_BYTES_PER_ROW = (1.445407e9 + 9.296896e6) / 1_799_944
 
 
 def log(*a):
