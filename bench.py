@@ -255,7 +255,7 @@ def run_wide(args):
         torch.cuda.empty_cache()
     print(json.dumps({"metric": "wide-block workloads: time to R, one call at a time", "unit": "ms",
                       "higher_is_better": False, "steps": args.steps, "warmup": args.warmup,
-                      "data": "synthetic (seeded)", "fp64_peak_tflops_derived": FP64_PEAK_TFLOPS,
+                      "data": "synthetic (seeded)", "fp64_peak_tflops_derived": FP64_PEAK_DERIVED,
                       "leaf_flops": "2 rows n^2 per block (Householder on the block's rows)",
                       "workloads": out}), flush=True)
 

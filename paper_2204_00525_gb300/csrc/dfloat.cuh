@@ -101,4 +101,44 @@ __device__ __forceinline__ dfl df_from_double(double x) {
 
 __device__ __forceinline__ double df_to_double(dfl a) { return (double)a.hi + (double)a.lo; }
 
+// hi + lo as a double with integer instructions only (the conversions above issue at the
+// FP64 rate).  hi's 24-bit significand is placed at bits 39-62 of a signed 64-bit integer S
+// and lo's is added at its own exponent (bits below bit 0 dropped), S is renormalised by at
+// most one left shift (hi a power of two, lo negative) and rounded to 53 bits (half up):
+// exact whenever the sum fits in 53 bits, which a normalised pair (|lo| <= ulp(hi) / 2, as
+// Fast2Sum leaves it) with lo at most 29 binades below hi's last bit does, and within one
+// unit in the last place otherwise.  Zero, subnormal, infinite or NaN parts and
+// unnormalised pairs take the conversions, out of line.
+static __device__ __noinline__ double df_to_double_wide(float hi, float lo) { return (double)hi + (double)lo; }
+
+__device__ __forceinline__ double df_to_double_int(float hi, float lo) {
+  const uint32_t hb = __float_as_uint(hi), lb = __float_as_uint(lo);
+  const int eh = (int)((hb >> 23) & 0xFFu), el = (int)((lb >> 23) & 0xFFu);
+  const bool lo_zero = (lb & 0x7FFFFFFFu) == 0u;
+  const int d = eh - (el == 0 ? 1 : el);          // binades between the two exponents
+  if (eh == 0 || eh == 255 || (!lo_zero && (el == 255 || d < 24))) return df_to_double_wide(hi, lo);
+  long long S = (long long)((hb & 0x7FFFFFu) | 0x800000u) << 39;
+  if (hb >> 31) S = -S;
+  if (!lo_zero) {
+    const long long L = (long long)((lb & 0x7FFFFFu) | (el ? 0x800000u : 0u));
+    const int sh = 39 - d;
+    const long long Lv = sh >= 0 ? (L << sh) : (sh > -24 ? (L >> -sh) : 0ll);
+    S += (lb >> 31) ? -Lv : Lv;
+  }
+  const unsigned long long sign = S < 0 ? 0x8000000000000000ull : 0ull;
+  unsigned long long M = (unsigned long long)(S < 0 ? -S : S);
+  int e = eh - 127 + 1023;
+  if (M < (1ull << 62)) {                        // one step below hi's binade
+    M <<= 1;
+    e -= 1;
+  }
+  M += 1ull << 9;                                // round bits 9..0 (half up)
+  if (M >= (1ull << 63)) {
+    M >>= 1;
+    e += 1;
+  }
+  M >>= 10;
+  return __longlong_as_double((long long)(sign | ((unsigned long long)e << 52) | (M & ((1ull << 52) - 1))));
+}
+
 }  // namespace fig

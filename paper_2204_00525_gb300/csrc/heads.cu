@@ -453,7 +453,7 @@ __global__ void k_heads_finish(LeafParams p, const int32_t* sizes, int mixed) {
     const int64_t c = k / G, g = k - c * G;
     double* h = p.heads + c * p.ldh + g;
     double s = *h;
-    if (mixed) s = (double)__int_as_float(__double2hiint(s)) + (double)__int_as_float(__double2loint(s));
+    if (mixed) s = df_to_double_int(__int_as_float(__double2hiint(s)), __int_as_float(__double2loint(s)));
     *h = s * p.hrow[g];
   }
 }
@@ -748,7 +748,7 @@ __global__ void k_gen_heads_finish(GenParams p) {
        k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = k / P, q = k - c * P;
     double s = p.data2[c * p.M + q];
-    if (p.gtails32) s = (double)__int_as_float(__double2hiint(s)) + (double)__int_as_float(__double2loint(s));
+    if (p.gtails32) s = df_to_double_int(__int_as_float(__double2hiint(s)), __int_as_float(__double2loint(s)));
     p.data2[c * p.M + q] = s * p.hf[q];
   }
 }
