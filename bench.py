@@ -197,7 +197,7 @@ def run_plan_only(args):
     dev_inputs = make_inputs(db, torch, "cuda")
     prec = binding.FIGARO_PREC_MIXED if args.plan_only.startswith("mixed") else binding.FIGARO_PREC_FP64
     p = binding.JoinPlan(dev_inputs, db.parent, precision=prec, stage_timing=args.plan_only.endswith("staged"),
-                         stream=torch.cuda.current_stream())
+                         stream=torch.cuda.current_stream(), fuse_tails=args.fuse_tails)
     p._R = torch.empty(db.n_cols, db.n_cols, dtype=torch.float64, device="cuda")
     ms = time_steps(p, torch, args.steps, args.warmup, lambda: None)
     p.close()
@@ -733,6 +733,8 @@ def main():
                     help="--impl reference: rows of the workload divided by this")
     ap.add_argument("--plan-only", choices=["fp64", "mixed", "fp64-staged", "mixed-staged"],
                     help="profiling aid: run one plan only and print no JSON line")
+    ap.add_argument("--fuse-tails", action="store_true",
+                    help="--plan-only: tails of relations with <= 32 columns formed inside the TSQR leaf")
     ap.add_argument("--workload", choices=["path3", "star", "snowflake", "snowflake-small"], default="snowflake",
                     help="workload of --plan-only")
     ap.add_argument("--wide", action="store_true",

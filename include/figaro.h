@@ -132,7 +132,15 @@ typedef struct figaro_join_tree {
  *                    the device).
  *   svd_max_sweeps   0 (default): 40; otherwise the largest number of Jacobi sweeps of
  *                    figaro_svd / figaro_pca / figaro_pca_centered before they give up
- *                    with FIGARO_ERR_TIMEOUT (not converged).                           */
+ *                    with FIGARO_ERR_TIMEOUT (not converged).
+ *   fuse_tails       0 (default): every tails block is written to device memory and then
+ *                    triangularised by the TSQR leaf.  1: the tails of a relation with at
+ *                    most 32 data columns (Def. "Head and Tail", Alg. 2) are formed in
+ *                    registers inside the TSQR leaf (§7 step 1) and never stored (not on
+ *                    FIGARO_PREC_MIXED_REFINED plans, nor under FIGARO_LEAF_GIVENS for
+ *                    blocks of <= 16 columns); the same R up to rounding, less device
+ *                    memory, about as fast (both halves are bound by arithmetic issue, not
+ *                    by memory bandwidth).  Any other value: INVALID_ARG.              */
 typedef struct figaro_options {
   int32_t precision;
   int32_t presorted;
@@ -143,7 +151,8 @@ typedef struct figaro_options {
   int32_t leaf;
   int32_t workspace_limit_mib;
   int32_t svd_max_sweeps;
-  int32_t reserved[7];
+  int32_t fuse_tails;
+  int32_t reserved[6];
 } figaro_options;
 
 typedef struct figaro_plan_s* figaro_plan_t;
@@ -313,7 +322,8 @@ int figaro_block_times(figaro_plan_t plan, int32_t max, double* leaf_ms, int32_t
  *                        Phi_circ of every group (group-major)
  *   FIGARO_DBG_PCOUNTS   uint64[2*P]: Phi_down, Phi_up of every X_p group
  *   FIGARO_DBG_TAILS     float64[(M-G) x N_i] column-major: sqrt(Phi_circ) T(S^{x})
- *                        of every group, groups in key order
+ *                        of every group, groups in key order (INVALID_ARG when the
+ *                        plan formed them inside the TSQR leaf: see fuse_tails)
  *   FIGARO_DBG_HEADS     float64[G x N_i] column-major: H(S^{x}) of every group
  *   FIGARO_DBG_GEN_TAILS float64[(G-P) x N_sub] column-major: generalized tails of
  *                        the projection (internal non-root relations)

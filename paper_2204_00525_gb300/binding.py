@@ -15,6 +15,7 @@ import os
 from . import build_lib
 
 FIGARO_OK = 0
+FIGARO_ERR_INVALID_ARG = 1
 FIGARO_ERR_OVERFLOW, FIGARO_ERR_NOMEM, FIGARO_ERR_TIMEOUT = 4, 5, 6
 FIGARO_ERR_UNSUPPORTED = 10
 FIGARO_KEY_I64, FIGARO_KEY_I32 = 0, 1
@@ -44,7 +45,7 @@ class figaro_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("presorted", C.c_int32), ("require_reduced", C.c_int32),
                 ("mem", C.c_int32), ("stage_timing", C.c_int32), ("gradients", C.c_int32),
                 ("leaf", C.c_int32), ("workspace_limit_mib", C.c_int32), ("svd_max_sweeps", C.c_int32),
-                ("reserved", C.c_int32 * 7)]
+                ("fuse_tails", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
 class figaro_plan_info(C.Structure):
@@ -222,7 +223,8 @@ class JoinPlan:
 
     def __init__(self, relations, parent, precision=FIGARO_PREC_FP64, presorted=False,
                  require_reduced=False, mem=FIGARO_MEM_DEVICE, stage_timing=False, stream=None,
-                 gradients=False, leaf=FIGARO_LEAF_HOUSEHOLDER, workspace_limit_mib=0, svd_max_sweeps=0):
+                 gradients=False, leaf=FIGARO_LEAF_HOUSEHOLDER, workspace_limit_mib=0, svd_max_sweeps=0,
+                 fuse_tails=False):
         import torch
         self._keep = []
         self._data = []
@@ -261,6 +263,7 @@ class JoinPlan:
         opt.leaf = int(leaf)
         opt.workspace_limit_mib = int(workspace_limit_mib)
         opt.svd_max_sweeps = int(svd_max_sweeps)
+        opt.fuse_tails = int(fuse_tails)
         self.mem = mem
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.handle = figaro_plan(tree, opt, self.stream.cuda_stream)

@@ -133,6 +133,7 @@ struct figaro_plan_s {
   // refinement of the mixed R (FIGARO_PREC_MIXED_REFINED)
   std::vector<double*> gram_partial;   // per block: per-CTA partial Gram matrices
   std::vector<const float*> block_lo32; // per block: low floats of its rows (tails blocks)
+  std::vector<fig::LeafParams> block_lp; // per block: the relation's pass parameters (fused tails blocks)
   double* gram = nullptr;              // A^T A (N x N)
   double* refine_w = nullptr;          // two N x N work arrays
   int* refine_ok = nullptr;            // device: 1 when the last refinement was applied
@@ -225,8 +226,10 @@ static void layout(figaro_plan_s& P, Arena& a) {
     b.lds = (M + 7) & ~int64_t(7);
     b.sdata = a.take<double>(b.lds * std::max(n.N, 1));
     b.heads = a.take<double>(M * std::max(n.N, 1));
-    b.tails = a.take<double>(M * std::max(n.N, 1));
-    b.tails32 = mixed ? a.take<float>(M * std::max(n.N, 1)) : nullptr;
+    // a tails block formed inside its leaf kernel is never stored
+    const bool fused = n.blk_tails >= 0 && P.blocks[n.blk_tails].fused;
+    b.tails = fused ? nullptr : a.take<double>(M * std::max(n.N, 1));
+    b.tails32 = (mixed && !fused) ? a.take<float>(M * std::max(n.N, 1)) : nullptr;
     b.tails32lo = refine ? a.take<float>(M * std::max(n.N, 1)) : nullptr;
     if (!n.leaf && !n.root) {
       b.data2 = a.take<double>(M * n.N_sub);
@@ -249,8 +252,11 @@ static void layout(figaro_plan_s& P, Arena& a) {
     b.tflag = a.take<uint8_t>(n.n_tiles * wide);
     b.tsum = a.take<double>(n.n_tiles * wide);
     b.tcarry = a.take<double>(n.n_tiles * wide);
-    b.lflag = a.take<uint8_t>(n.n_tiles * wide * 32);
-    b.lsum = a.take<double>(n.n_tiles * wide * 32);
+    b.ltcarry = a.take<double>(n.n_tiles * std::max(n.N, 1));
+    b.lflag = a.take<uint8_t>(n.n_tiles * std::max(n.N_sub, 1) * 32);
+    b.lsum = a.take<double>(n.n_tiles * std::max(n.N_sub, 1) * 32);
+    b.llflag = a.take<uint8_t>(n.n_tiles * std::max(n.N, 1) * 32);
+    b.llsum = a.take<double>(n.n_tiles * std::max(n.N, 1) * 32);
     b.coldesc = a.take<int2>(std::max(n.N_sub, 1));
     if (P.opt.gradients) {
       n.g_up = a.take<double>((int64_t)P.N * n.pbound);
@@ -553,6 +559,8 @@ static void make_blocks(figaro_plan_s& P) {
       t.kind = BLK_TAILS;
       t.M = n.M;
       t.bound = n.M;
+      // formed inside the leaf where tsqr_plan_block allows it (<= 32 columns, Householder)
+      t.fused = P.opt.precision != FIGARO_PREC_MIXED_REFINED && P.opt.fuse_tails;
       tsqr_plan_block(t, mixed, P.opt.leaf == FIGARO_LEAF_GIVENS, P.opt.leaf != FIGARO_LEAF_MMA_SYNC);
       P.blocks.push_back(t);
       P.stack_rows += t.n;
@@ -598,6 +606,7 @@ static void bind_blocks(figaro_plan_s& P) {
   P.stack_blk.err = P.err_dev;
   size_t bi = 0;
   P.block_lo32.assign(P.blocks.size(), nullptr);
+  P.block_lp.assign(P.blocks.size(), fig::LeafParams{});
   for (auto& n : P.nodes) {
     if (n.N > 0) {
       P.block_lo32[bi] = n.b.tails32lo;
@@ -709,7 +718,8 @@ static int enqueue_r(figaro_plan_s& P, double* R, int64_t ldr) {
     FIG_CUDA(wait(s, ready));
     if (serial) FIG_CUDA(cudaEventRecord(P.leaf_ev[2 * bi], s));
     const int64_t l0 = P.launches;
-    tsqr_leaf(P.blocks[bi], mixed, s, &P.launches);
+    if (P.blocks[bi].fused) tails_qr(P.block_lp[bi], P.blocks[bi], s, &P.launches);
+    else tsqr_leaf(P.blocks[bi], mixed, s, &P.launches);
     P.stage_launch[5] += P.launches - l0;
     if (serial) FIG_CUDA(cudaEventRecord(P.leaf_ev[2 * bi + 1], s));
     tsqr_reduce(P.blocks[bi], mixed, s, &P.launches);
@@ -823,6 +833,8 @@ static int enqueue_r(figaro_plan_s& P, double* R, int64_t ldr) {
     lp.hrow = n.b.hrow;
     lp.beta = P.beta;
     lp.beta_len = P.beta_len;
+    const bool fused = n.blk_tails >= 0 && P.blocks[n.blk_tails].fused;
+    lp.mixed = mixed;
     lp.tails = n.b.tails;
     lp.tails32 = mixed ? n.b.tails32 : nullptr;
     lp.tails32lo = refine ? n.b.tails32lo : nullptr;
@@ -831,9 +843,11 @@ static int enqueue_r(figaro_plan_s& P, double* R, int64_t ldr) {
     lp.ldh = n.M;
     lp.tflag = n.b.tflag;
     lp.tsum = n.b.tsum;
-    lp.tcarry = n.b.tcarry;
-    lp.lflag = n.b.lflag;
-    lp.lsum = n.b.lsum;
+    lp.tcarry = n.b.ltcarry;
+    // lane partials for the stored tails pass and for a fused leaf with the first pass's
+    // lanes (8 rows each: blocks of <= 8 columns); wider fused leaves scan their lanes
+    lp.lflag = (fused && P.blocks[n.blk_tails].nreg > 8) ? nullptr : n.b.llflag;
+    lp.lsum = n.b.llsum;
     lp.n_tiles = n.n_tiles;
     if (n.b.sperm && row_gather_pays(n.M, n.N)) {   // the sorted copy, by whole rows
       if (n.layout == FIGARO_COL_MAJOR) {
@@ -844,7 +858,9 @@ static int enqueue_r(figaro_plan_s& P, double* R, int64_t ldr) {
       }
       lp.sorted_ready = 1;
     }
-    leaf_heads_tails(lp, n.b.sizes, s, &P.launches);
+    leaf_heads(lp, n.b.sizes, s, &P.launches);
+    if (fused) P.block_lp[n.blk_tails] = lp;
+    else leaf_tails(lp, s, &P.launches);
     FIG_CUDA(rec(P.ev_leaf[i], s));
     if (!serial && n.blk_tails >= 0) {
       const int rc = run_block(n.blk_tails, P.ev_leaf[i]);
@@ -1094,6 +1110,10 @@ int figaro_plan(const figaro_join_tree* tree, const figaro_options* opt, void* s
   if (P->opt.mem != FIGARO_MEM_DEVICE && P->opt.mem != FIGARO_MEM_HOST) {
     delete P;
     return fail(FIGARO_ERR_INVALID_ARG, "mem");
+  }
+  if (P->opt.fuse_tails != 0 && P->opt.fuse_tails != 1) {
+    delete P;
+    return fail(FIGARO_ERR_INVALID_ARG, "fuse_tails");
   }
   if (P->opt.workspace_limit_mib < 0 || P->opt.svd_max_sweeps < 0) {
     delete P;
@@ -1746,7 +1766,9 @@ int64_t figaro_debug_read(figaro_plan_t p, int32_t rel, int32_t what, void* dst,
       }
       return need;
     }
-    case FIGARO_DBG_TAILS: return copy2d(n.b.tails, n.M - G, n.N, n.M, 8);
+    case FIGARO_DBG_TAILS:
+      if (!n.b.tails) return -FIGARO_ERR_INVALID_ARG;   // formed in the leaf, never stored
+      return copy2d(n.b.tails, n.M - G, n.N, n.M, 8);
     case FIGARO_DBG_HEADS: return copy2d(n.b.heads, G, n.N, n.M, 8);
     case FIGARO_DBG_GEN_TAILS:
       if (n.leaf || n.root) return 0;

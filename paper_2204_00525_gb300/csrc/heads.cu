@@ -23,22 +23,9 @@
 //   head: P_n / sqrt(W_n) with W_n = Phi_down(x_p).
 #include "dfloat.cuh"
 #include "kernels.cuh"
+#include "leaf.cuh"
 
 namespace fig {
-
-// (f, s): f = a segment starts inside the range, s = sum after its last start (or the
-// whole range when f == 0).  combine(earlier, later).
-__device__ __forceinline__ void pair_scan_incl(int& f, double& s, int lane) {
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int fo = __shfl_up_sync(0xffffffffu, f, o);
-    double so = __shfl_up_sync(0xffffffffu, s, o);
-    if (lane >= o) {
-      s = f ? s : so + s;
-      f |= fo;
-    }
-  }
-}
 
 // Per-position coefficients of the tail formula, {beta_p, p beta_p} with
 // beta_p = 1 / sqrt(p (p + 1)), for every position p of every group (the table's length
@@ -182,62 +169,7 @@ void rows_gather(const double* rows, int64_t rs, const int32_t* perm, int64_t M,
 }
 
 // ------------------------------------------------------------------ relations (v = 1)
-struct LeafRow {
-  int32_t src;   // input row
-  int32_t pos;   // position inside the group
-  int32_t g;
-  bool ok, last;
-};
-
-__device__ __forceinline__ LeafRow leaf_row(const LeafParams& p, int64_t e) {
-  LeafRow r;
-  r.ok = e < p.M;
-  if (!r.ok) { r.src = 0; r.pos = 1; r.g = 0; r.last = false; return r; }
-  r.src = p.perm ? p.perm[e] : (int32_t)e;
-  r.g = p.row_gid[e];
-  const int32_t start = p.goff[r.g];
-  r.pos = (int32_t)(e - start);
-  r.last = (e == (int64_t)p.goff[r.g + 1] - 1);
-  return r;
-}
-
-// The kHtItems values of column c for one lane's consecutive sorted rows: gathered through
-// the permutation (first pass; a copy in sorted order is kept when p.sdata is set), or read
-// back from that copy (last pass) with 16-byte loads.
-__device__ __forceinline__ void load_leaf_items(const LeafParams& p, const LeafRow (&rw)[kHtItems], int64_t e0,
-                                                int c, bool from_copy, double (&xs)[kHtItems]) {
-  if (from_copy) {
-    const double* col = p.sdata + (int64_t)c * p.lds + e0;
-    if (e0 + kHtItems <= p.M) {
-#pragma unroll
-      for (int i = 0; i < kHtItems; i += 2) {
-        const double2 v = *reinterpret_cast<const double2*>(col + i);
-        xs[i] = v.x;
-        xs[i + 1] = v.y;
-      }
-    } else {
-#pragma unroll
-      for (int i = 0; i < kHtItems; ++i) xs[i] = rw[i].ok ? col[i] : 0.0;
-    }
-    return;
-  }
-#pragma unroll
-  for (int i = 0; i < kHtItems; ++i) xs[i] = rw[i].ok ? p.data[(int64_t)rw[i].src * p.rs + (int64_t)c * p.cs] : 0.0;
-  if (p.sdata) {
-    double* col = p.sdata + (int64_t)c * p.lds + e0;
-    if (e0 + kHtItems <= p.M) {
-#pragma unroll
-      for (int i = 0; i < kHtItems; i += 2) *reinterpret_cast<double2*>(col + i) = make_double2(xs[i], xs[i + 1]);
-    } else {
-#pragma unroll
-      for (int i = 0; i < kHtItems; ++i)
-        if (rw[i].ok) col[i] = xs[i];
-    }
-  }
-}
-
-// Pass 1: per tile and column, the tile aggregate (for the carry scan) and every lane's
-// exclusive (flag, sum) inside the tile, so that pass 3 needs no cross-lane work.
+// Every lane's exclusive (flag, sum) inside the tile and the tile aggregate (lane 31).
 __device__ __forceinline__ void store_lane_and_tile(int f, double s, int lane, int64_t slot, int64_t tslot,
                                                     uint8_t* lflag, double* lsum, uint8_t* tflag, double* tsum) {
   pair_scan_incl(f, s, lane);
@@ -252,7 +184,14 @@ __device__ __forceinline__ void store_lane_and_tile(int f, double s, int lane, i
   }
 }
 
-__global__ void __launch_bounds__(256) k_leaf_agg(LeafParams p) {
+// Pass 1: per tile and column, the tile aggregate (for the carry scan), every lane's
+// exclusive (flag, sum) inside the tile when a tails pass follows (lflag set), and every
+// group's sum from its start or from the start of the tile holding its last row, written
+// at the group's head (k_heads_finish adds the carry of groups that began in an earlier
+// tile), so that the heads need no later pass over the data.  The running sum of the lane
+// is that sum for every group that begins in the lane; only the lane's first group, when
+// it began in an earlier lane, waits for the lane's exclusive prefix.
+__global__ void __launch_bounds__(256, 3) k_leaf_agg(LeafParams p) {
   const int lane = threadIdx.x & 31;
   const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -266,20 +205,39 @@ __global__ void __launch_bounds__(256) k_leaf_agg(LeafParams p) {
       load_leaf_items(p, rw, e0, c, p.sorted_ready != 0, xs);
       int f = 0;
       double s = 0.0;
+      int open_g = -1;                     // a group that ends in this lane but began before it
+      double open_s = 0.0;
 #pragma unroll
       for (int i = 0; i < kHtItems; ++i) {
         if (!rw[i].ok) continue;
         const double x = xs[i];
         if (rw[i].pos == 0) { f = 1; s = x; } else { s += x; }
+        if (rw[i].last) {
+          if (f) p.heads[(int64_t)c * p.ldh + rw[i].g] = s;
+          else { open_g = rw[i].g; open_s = s; }
+        }
       }
+      pair_scan_incl(f, s, lane);
+      int fe = __shfl_up_sync(0xffffffffu, f, 1);
+      double se = __shfl_up_sync(0xffffffffu, s, 1);
+      if (lane == 0) { fe = 0; se = 0.0; }
       const int64_t slot = (int64_t)c * p.n_tiles + t;
-      store_lane_and_tile(f, s, lane, slot, slot, p.lflag, p.lsum, p.tflag, p.tsum);
+      if (p.lflag) {
+        p.lflag[slot * 32 + lane] = (uint8_t)fe;
+        p.lsum[slot * 32 + lane] = se;
+      }
+      if (lane == 31) {
+        p.tflag[slot] = (uint8_t)f;
+        p.tsum[slot] = s;
+      }
+      if (open_g >= 0) p.heads[(int64_t)c * p.ldh + open_g] = se + open_s;
     }
   }
 }
 
-// Pass 3: the running sum of every lane starts at its carry (tile carry combined with the
-// lane's exclusive partial), so each cell costs one add, one FMA and one multiply.
+// Pass 3 (tails blocks that are materialised): the running sum of every lane starts at its
+// carry (tile carry combined with the lane's exclusive partial), so each cell costs one
+// add, one FMA and one multiply.
 __global__ void __launch_bounds__(256, 2) k_leaf_emit(LeafParams p) {
   const int lane = threadIdx.x & 31;
   const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -311,7 +269,6 @@ __global__ void __launch_bounds__(256, 2) k_leaf_emit(LeafParams p) {
         if (rw[i].pos == 0) run = 0.0;
         if (rw[i].pos > 0) tcol[e0 + i - rw[i].g - 1] = fma(ca[i], x, -(cb[i] * run));
         run += x;
-        if (rw[i].last) p.heads[(int64_t)c * p.ldh + rw[i].g] = run;   // group sum; scaled by heads_finish
       }
     }
   }
@@ -323,30 +280,7 @@ __global__ void __launch_bounds__(256, 2) k_leaf_emit(LeafParams p) {
 // p a_p - S_p is formed in double-float, and the tail row is rounded once to float for
 // the FP32 TSQR leaf.  Heads stay float64.  Carries between lanes and tiles are kept in
 // float64 (one conversion per lane and column).
-__device__ __forceinline__ void pair_scan_incl_df(int& f, dfl& s, int lane) {
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int fo = __shfl_up_sync(0xffffffffu, f, o);
-    const float sh = __shfl_up_sync(0xffffffffu, s.hi, o);
-    const float sl = __shfl_up_sync(0xffffffffu, s.lo, o);
-    if (lane >= o) {
-      if (!f) s = df_add(dfl{sh, sl}, s);
-      f |= fo;
-    }
-  }
-}
-
-__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
-  const float p = a.hi * b.hi;
-  float e = fmaf(a.hi, b.hi, -p);
-  e = fmaf(a.hi, b.lo, e);
-  e = fmaf(a.lo, b.hi, e);
-  dfl r;
-  fast_two(p, e, r.hi, r.lo);
-  return r;
-}
-
-__global__ void __launch_bounds__(256) k_leaf_agg_mx(LeafParams p) {
+__global__ void __launch_bounds__(256, 3) k_leaf_agg_mx(LeafParams p) {
   const int lane = threadIdx.x & 31;
   const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -360,22 +294,36 @@ __global__ void __launch_bounds__(256) k_leaf_agg_mx(LeafParams p) {
       load_leaf_items(p, rw, e0, c, p.sorted_ready != 0, xs);
       int f = 0;
       dfl s{0.0f, 0.0f};
+      int open_g = -1;                     // as in k_leaf_agg
+      dfl open_s{0.0f, 0.0f};
 #pragma unroll
       for (int i = 0; i < kHtItems; ++i) {
         if (!rw[i].ok) continue;
         const dfl x = df_from_double(xs[i]);
         if (rw[i].pos == 0) { f = 1; s = x; } else { s = df_add(s, x); }
+        // group sums stored as the pair's bits (combined by heads_finish: a conversion here
+        // would be if-converted and issued for every element)
+        if (rw[i].last) {
+          if (f) p.heads[(int64_t)c * p.ldh + rw[i].g] = __hiloint2double(__float_as_int(s.hi), __float_as_int(s.lo));
+          else { open_g = rw[i].g; open_s = s; }
+        }
       }
       pair_scan_incl_df(f, s, lane);
       int fe = __shfl_up_sync(0xffffffffu, f, 1);
       float eh = __shfl_up_sync(0xffffffffu, s.hi, 1), el = __shfl_up_sync(0xffffffffu, s.lo, 1);
       if (lane == 0) { fe = 0; eh = 0.0f; el = 0.0f; }
       const int64_t slot = (int64_t)c * p.n_tiles + t;
-      p.lflag[slot * 32 + lane] = (uint8_t)fe;
-      p.lsum[slot * 32 + lane] = df_to_double(dfl{eh, el});
+      if (p.lflag) {
+        p.lflag[slot * 32 + lane] = (uint8_t)fe;
+        p.lsum[slot * 32 + lane] = df_to_double(dfl{eh, el});
+      }
       if (lane == 31) {
         p.tflag[slot] = (uint8_t)f;
         p.tsum[slot] = df_to_double(s);
+      }
+      if (open_g >= 0) {
+        const dfl h = df_add(dfl{eh, el}, open_s);
+        p.heads[(int64_t)c * p.ldh + open_g] = __hiloint2double(__float_as_int(h.hi), __float_as_int(h.lo));
       }
     }
   }
@@ -426,10 +374,6 @@ __global__ void __launch_bounds__(256, LO ? 2 : 3) k_leaf_emit_mx(LeafParams p) 
           }
         }
         run = df_add(run, x);
-        // the pair's bits, combined and scaled by heads_finish (a conversion here would be
-        // if-converted and issued for every element)
-        if (rw[i].last)
-          p.heads[(int64_t)c * p.ldh + rw[i].g] = __hiloint2double(__float_as_int(run.hi), __float_as_int(run.lo));
       }
     }
   }
@@ -443,32 +387,55 @@ static unsigned ht_grid(int64_t n_tiles) {
   return (unsigned)blocks;
 }
 
-// Head of every group: the group sum written by the last pass (a float pair's bits on
-// the mixed path) times 1 / sqrt(rows).
+// Head of every group: the partial sum written by the first pass (a float pair's bits on
+// the mixed path), plus the carry of the tile holding the group's last row when the group
+// began in an earlier tile, times 1 / sqrt(rows).  One thread per group walks the columns,
+// so the group's offsets and scale are read once.
 __global__ void k_heads_finish(LeafParams p, const int32_t* sizes, int mixed) {
   const int64_t G = sizes[0];
-  const int64_t total = G * p.N;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = k / G, g = k - c * G;
-    double* h = p.heads + c * p.ldh + g;
-    double s = *h;
-    if (mixed) s = df_to_double_int(__int_as_float(__double2hiint(s)), __int_as_float(__double2loint(s)));
-    *h = s * p.hrow[g];
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < G; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = ((int64_t)p.goff[g + 1] - 1) / kHtTile;
+    const bool carry = (int64_t)p.goff[g] < t * kHtTile;
+    const double hr = p.hrow[g];
+    // four columns at a time, every load before the first store (the stores may alias the
+    // loads as far as the compiler knows, which would otherwise serialise the columns)
+    for (int c0 = 0; c0 < p.N; c0 += 4) {
+      double s[4], cy[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int c = c0 + i;
+        s[i] = c < p.N ? p.heads[(int64_t)c * p.ldh + g] : 0.0;
+        cy[i] = (carry && c < p.N) ? p.tcarry[(int64_t)c * p.n_tiles + t] : 0.0;
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int c = c0 + i;
+        if (c >= p.N) break;
+        double v = s[i];
+        if (mixed) v = df_to_double_int(__int_as_float(__double2hiint(v)), __int_as_float(__double2loint(v)));
+        p.heads[(int64_t)c * p.ldh + g] = (v + cy[i]) * hr;
+      }
+    }
   }
 }
 
-void leaf_heads_tails(const LeafParams& p, const int32_t* sizes, cudaStream_t st, int64_t* launches) {
+void leaf_heads(const LeafParams& p, const int32_t* sizes, cudaStream_t st, int64_t* launches) {
   if (p.N == 0) return;
   const unsigned g = ht_grid(p.n_tiles);
-  if (p.tails32) k_leaf_agg_mx<<<g, 256, 0, st>>>(p);
+  if (p.mixed) k_leaf_agg_mx<<<g, 256, 0, st>>>(p);
   else k_leaf_agg<<<g, 256, 0, st>>>(p);
   k_tile_carry<<<p.N, kCarryThreads, 0, st>>>(p.tflag, p.tsum, p.tcarry, p.n_tiles, nullptr);
-  if (p.tails32 && p.tails32lo) k_leaf_emit_mx<true><<<g, 256, 0, st>>>(p);
-  else if (p.tails32) k_leaf_emit_mx<false><<<g, 256, 0, st>>>(p);
+  k_heads_finish<<<grid_for(p.M, 256, 152 * 8), 256, 0, st>>>(p, sizes, p.mixed);
+  *launches += 3;
+}
+
+void leaf_tails(const LeafParams& p, cudaStream_t st, int64_t* launches) {
+  if (p.N == 0) return;
+  const unsigned g = ht_grid(p.n_tiles);
+  if (p.mixed && p.tails32lo) k_leaf_emit_mx<true><<<g, 256, 0, st>>>(p);
+  else if (p.mixed) k_leaf_emit_mx<false><<<g, 256, 0, st>>>(p);
   else k_leaf_emit<<<g, 256, 0, st>>>(p);
-  k_heads_finish<<<grid_for(p.M * (int64_t)p.N, 256, 152 * 8), 256, 0, st>>>(p, sizes, p.tails32 != nullptr);
-  *launches += 4;
+  ++*launches;
 }
 
 // ------------------------------------------------------------------ join + projection

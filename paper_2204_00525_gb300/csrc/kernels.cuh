@@ -61,8 +61,12 @@ struct NodeBuf {
   uint8_t* tflag;       // [n_tiles * max(N_i, N_sub)]
   double* tsum;
   double* tcarry;
-  uint8_t* lflag;       // [n_tiles * max(N_i, N_sub) * 32]: lane exclusive partials
+  double* ltcarry;      // tile carries of the relation pass (a fused leaf reads them while the
+                        // generalized pass of the same node uses tflag/tsum/tcarry)
+  uint8_t* lflag;       // [n_tiles * N_sub * 32]: lane exclusive partials of the generalized pass
   double* lsum;
+  uint8_t* llflag;      // [n_tiles * N_i * 32]: those of the relation pass (a fused leaf reads
+  double* llsum;        //   them while the generalized pass runs)
   int2* coldesc;        // [N_sub] (source kind, source column) for the join
 };
 
@@ -148,6 +152,7 @@ struct LeafParams {
   float* tails32;            // mixed precision: float tails (leading dimension ldt) instead of tails
   float* tails32lo;          // with tails32, optional: the low parts (tail = tails32 + tails32lo)
   int sorted_ready;          // 1: sdata already holds the data in sorted order (k_rows_gather)
+  int mixed;                 // mixed precision: double-float prefix sums, float tails
   double* heads;
   int64_t ldh;
   uint8_t* tflag;
@@ -203,7 +208,10 @@ inline int row_pitch(int cols) { return (cols + 1) & ~1; }
 // copy out) against N sectors of 32 bytes for the plain gather, part of which hit L2 while
 // the table is not much larger than L2: they pay for tables of 1 GiB and more.
 inline bool row_gather_pays(int64_t rows, int cols) { return cols > 0 && (double)rows * cols * 8.0 >= 1073741824.0; }
-void leaf_heads_tails(const LeafParams& p, const int32_t* sizes, cudaStream_t st, int64_t* launches);
+// Heads of a relation (first pass, tile carries, heads_finish) and, for tails blocks that
+// are materialised, the tails (last pass).
+void leaf_heads(const LeafParams& p, const int32_t* sizes, cudaStream_t st, int64_t* launches);
+void leaf_tails(const LeafParams& p, cudaStream_t st, int64_t* launches);
 void gen_heads_tails(const GenParams& p, cudaStream_t st, int64_t* launches);
 
 // ------------------------------------------------------------------ tsqr.cu
@@ -237,6 +245,7 @@ struct TsqrBlock {
   bool fold_tc;              // fold path, float leaf: panels with tensor-core trailing updates
   bool fold_tc5;             // fold path, float leaf on tcgen05 (k_tsqr_fold_tc, 128-row chunks)
   int* err;                  // the plan's device error word (bounded waits report TIMEOUT)
+  bool fused;                // tails block formed inside its leaf kernel (tails_qr): rows = M sorted rows
 };
 
 // tsqr_tc.cu: the float leaf on the 5th-generation tensor cores
@@ -246,6 +255,9 @@ void launch_fold_tc(const TsqrBlock& b, double* tri_out, int* err, cudaStream_t 
 cudaError_t fold_tc_set_attributes();
 
 void tsqr_plan_block(TsqrBlock& b, bool mixed, bool givens = false, bool tcgen05 = false);
+// tails_qr_f64.cu: the tails of a relation with <= 32 data columns formed in registers and
+// triangularised by the leaf (the block's tri[0]), after leaf_heads has made the carries
+void tails_qr(const LeafParams& p, const TsqrBlock& b, cudaStream_t st, int64_t* launches);
 int64_t tsqr_tri_elems(const TsqrBlock& b);
 int64_t tsqr_scratch_elems(const TsqrBlock& b, bool mixed);
 void tsqr_leaf(const TsqrBlock& b, bool mixed, cudaStream_t st, int64_t* launches);

@@ -201,10 +201,10 @@ __global__ void __launch_bounds__(1024) k_refine(double* R, int64_t ldr, const d
         if (!(p > 0.0) || !isfinite(p)) {
           bad = 1;
         } else {
-          double beta, v0, tau;                       // 1 / sqrt(p) by the Newton steps of
-          HhScalars<double>::get(0.0, p, beta, v0, tau);   // the Householder scalars:
-          rinv[0] = -beta;                            // nu = sqrt(p), tau = 1 / p
-          rinv[1] = -beta * tau;                      // 1 / sqrt(p)
+          double beta, v0, tau, tau2;                 // 1 / sqrt(p) by the Newton steps of
+          HhScalars<double>::get(0.0, p, beta, v0, tau, tau2);   // the Householder scalars:
+          rinv[0] = -beta;                            // nu = sqrt(p), tau tau2 = 1 / p
+          rinv[1] = -beta * tau * tau2;               // 1 / sqrt(p)
         }
       }
       __syncthreads();

@@ -111,10 +111,10 @@ __device__ void hh_small(E* A, int lda, int m, int n, E* red) {
         E* aj = A + (int64_t)(mine ? j : k) * lda;
         const E akj = mine ? aj[k] : E(0);
         __syncwarp();                            // every read of row k before its writes
-        E beta, v0, tau;
-        HhScalars<E>::get(alpha, sigma, beta, v0, tau);
+        E beta, v0, tau, tau2;
+        HhScalars<E>::get(alpha, sigma, beta, v0, tau, tau2);
         if (mine) {
-          wj = tau * fma(v0, akj, dj);
+          wj = tau * fma(v0, akj, dj) * tau2;
           aj[k] = akj - wj * v0;
         }
         if (lane == 0) A[(int64_t)k * lda + k] = beta;
@@ -1048,6 +1048,7 @@ void tsqr_plan_block(TsqrBlock& b, bool mixed, bool givens, bool tcgen05) {
   const size_t esz = mixed ? sizeof(float) : sizeof(double);
   b.nreg = reg_class(n);
   b.givens = givens && b.nreg && b.nreg <= 16;
+  b.fused = b.fused && b.kind == BLK_TAILS && b.nreg && !b.givens;
   if (b.nreg) {
     // one warp's QR of a tile costs about N^2 FP64 instructions at ~70 cycles each: for
     // N <= 16 (tiles of 128-256 rows) it beats a thread block per tile from two tiles
@@ -1058,6 +1059,8 @@ void tsqr_plan_block(TsqrBlock& b, bool mixed, bool givens, bool tcgen05) {
     // their trees with the block-per-tile kernel only, six triangles at a time
     b.fan = b.nreg <= 16 ? b.tile / n : 6;
     if (b.givens) b.tile = kGivensRows;       // leaf chunks of the Givens leaf
+    // tails formed in the leaf (tails_qr): QR tiles of 32 lanes x 8, 4 or 2 sorted rows
+    else if (b.fused) b.tile = 32 * (b.nreg <= 8 ? 8 : b.nreg <= 16 ? 4 : 2);
   } else if (fold_plan(b, mixed, esz, tcgen05)) {
     return;
   } else {
@@ -1203,7 +1206,9 @@ void tsqr_reduce(TsqrBlock& b, bool mixed, cudaStream_t st, int64_t* launches) {
 void tsqr_final(const TsqrBlock* blocks_dev, int n_blocks, TsqrBlock& stack_blk, double* R, int64_t ldr,
                 cudaStream_t st, int64_t* launches) {
   const int N = stack_blk.n;
-  if (N <= kFoldWorkers) {
+  // Up to 32 columns the dense stack goes through the register leaf in a launch or two,
+  // which beats the fold's single block walking the pieces one Householder step at a time.
+  if (N > 32 && N <= kFoldWorkers) {
     int mc = 0, tsm = 0;
     size_t smem = 0;
     stack_fold_plan(N, mc, tsm, smem);

@@ -10,7 +10,7 @@ __device__ __forceinline__ int64_t block_rows(const TsqrBlock& b) {
   if (b.kind == BLK_FIXED) return b.M;
   const int32_t G = b.sizes[0], P = b.sizes[1];
   switch (b.kind) {
-    case BLK_TAILS: return b.M - G;
+    case BLK_TAILS: return b.fused ? b.M : b.M - G;
     case BLK_GEN: return (int64_t)G - P;
     default: return G;
   }
@@ -39,14 +39,19 @@ __device__ __forceinline__ bool copy_single(const TsqrBlock& b, int64_t rows, in
 // Scalars of one Householder step: the reflector maps x = (alpha, a_{k+1..m-1,k}) with
 // sigma = sum_{i>k} a_ik^2 to (beta, 0, ..., 0): nu = ||x||, beta = -sign(alpha) nu,
 // v0 = alpha - beta (v = (v0, a_{k+1..m-1,k}) unnormalised) and
-// tau = 2 / (v^T v) = 1 / (nu (nu + |alpha|)).
+// tau = 2 / (v^T v) = 1 / (nu (nu + |alpha|)), returned as the product tau * tau2 of two
+// factors: a column that holds only rounding residue (a tile with fewer independent rows
+// than columns, reflected again at every later step) shrinks towards the format's smallest
+// numbers, where 1 / (nu (nu + |alpha|)) overflows although 1 / nu and 1 / (nu + |alpha|)
+// do not; the caller scales by both.
 template <typename E>
 struct HhScalars {
-  __device__ static void get(E alpha, E sigma, E& beta, E& v0, E& tau) {
+  __device__ static void get(E alpha, E sigma, E& beta, E& v0, E& tau, E& tau2) {
     const E nu = sqrt(fma(alpha, alpha, sigma));
     beta = alpha >= E(0) ? -nu : nu;
     v0 = alpha - beta;
-    tau = E(1) / (nu * (nu + fabs(alpha)));
+    tau = E(1) / nu;
+    tau2 = E(1) / (nu + fabs(alpha));
   }
 };
 
@@ -58,10 +63,12 @@ struct HhScalars {
 // float seeds are moved between the formats by exponent arithmetic on the bit patterns
 // (conversions, comparisons and sign tests would each take an FP64 issue slot), which
 // is exact for the normal values of the range tested first; outside it (|t| beyond
-// 2^+-100) the plain operations are used.
-static __device__ __noinline__ void hh_scalars_wide(double alpha, double sigma, double& nu, double& tau) {
+// 2^+-100) the plain operations are used, with tau in two factors.
+static __device__ __noinline__ void hh_scalars_wide(double alpha, double sigma, double& nu, double& tau,
+                                                    double& tau2) {
   nu = sqrt(fma(alpha, alpha, sigma));
-  tau = 1.0 / (nu * (nu + fabs(alpha)));
+  tau = 1.0 / nu;
+  tau2 = 1.0 / (nu + fabs(alpha));
 }
 
 // float nearest below a positive normal double whose exponent is within float range
@@ -89,9 +96,10 @@ __device__ __forceinline__ bool f64_mid_range(double x) {
 
 template <>
 struct HhScalars<double> {
-  __device__ static void get(double alpha, double sigma, double& beta, double& v0, double& tau) {
+  __device__ static void get(double alpha, double sigma, double& beta, double& v0, double& tau, double& tau2) {
     const double t = fma(alpha, alpha, sigma);
     double nu;
+    tau2 = 1.0;
     if (f64_mid_range(t)) {
       double y = f64_of_f32_bits(rsqrtf(f32_of_f64_bits(t)));
       const double ht = 0.5 * t;
@@ -103,7 +111,7 @@ struct HhScalars<double> {
       r = r * fma(-d, r, 2.0);
       tau = r * fma(-d, r, 2.0);
     } else {
-      hh_scalars_wide(alpha, sigma, nu, tau);
+      hh_scalars_wide(alpha, sigma, nu, tau, tau2);
     }
     beta = __double_as_longlong(alpha) >= 0 ? -nu : nu;     // sign bit: no FP64 compare
     v0 = alpha - beta;
@@ -202,8 +210,8 @@ __device__ __forceinline__ void reg_hh_step(E (&a)[RPL][N], int m, int lane) {
   if (f64_is_zero(sig)) return;              // uniform: column already reduced below K
   constexpr int kr = K / 32, kl = K % 32;    // lane and slot holding row K
   const E alpha = __shfl_sync(0xffffffffu, a[kr][K], kl);
-  E beta, v0, tau;
-  HhScalars<E>::get(alpha, sig, beta, v0, tau);
+  E beta, v0, tau, tau2;
+  HhScalars<E>::get(alpha, sig, beta, v0, tau, tau2);
   const int my_t = lane >> (5 - Log2<P2>::v);   // the value this lane holds
   E akt = E(0);
 #pragma unroll
@@ -211,7 +219,7 @@ __device__ __forceinline__ void reg_hh_step(E (&a)[RPL][N], int m, int lane) {
     const E v = __shfl_sync(0xffffffffu, a[kr][K + t], kl);
     if (my_t == t) akt = v;
   }
-  const E w_mine = tau * fma(v0, akt, mine);
+  const E w_mine = tau * fma(v0, akt, mine) * tau2;
   if (lane == kl) x[kr] = v0;
 #pragma unroll
   for (int t = 1; t < C; ++t) {
