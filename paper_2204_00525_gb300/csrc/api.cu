@@ -858,7 +858,7 @@ static int enqueue_r(figaro_plan_s& P, double* R, int64_t ldr) {
       }
       lp.sorted_ready = 1;
     }
-    leaf_heads(lp, n.b.sizes, s, &P.launches);
+    leaf_heads(lp, s, &P.launches);
     if (fused) P.block_lp[n.blk_tails] = lp;
     else leaf_tails(lp, s, &P.launches);
     FIG_CUDA(rec(P.ev_leaf[i], s));

@@ -185,12 +185,13 @@ __device__ __forceinline__ void store_lane_and_tile(int f, double s, int lane, i
 }
 
 // Pass 1: per tile and column, the tile aggregate (for the carry scan), every lane's
-// exclusive (flag, sum) inside the tile when a tails pass follows (lflag set), and every
-// group's sum from its start or from the start of the tile holding its last row, written
-// at the group's head (k_heads_finish adds the carry of groups that began in an earlier
-// tile), so that the heads need no later pass over the data.  The running sum of the lane
-// is that sum for every group that begins in the lane; only the lane's first group, when
-// it began in an earlier lane, waits for the lane's exclusive prefix.
+// exclusive (flag, sum) inside the tile when a tails pass follows (lflag set), and the head
+// of every group that begins in the tile (its sum times 1 / sqrt(rows)), so that the heads
+// need no later pass over the data.  The running sum of the lane is the group's sum for
+// every group that begins in the lane; only the lane's first group, when it began in an
+// earlier lane, waits for the lane's exclusive prefix.  A group that began in an earlier
+// tile (at most one ends in each tile) gets its sum from the tile start, and k_heads_fix
+// adds the tile's carry and scales it.
 __global__ void __launch_bounds__(256, 3) k_leaf_agg(LeafParams p) {
   const int lane = threadIdx.x & 31;
   const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -213,7 +214,7 @@ __global__ void __launch_bounds__(256, 3) k_leaf_agg(LeafParams p) {
         const double x = xs[i];
         if (rw[i].pos == 0) { f = 1; s = x; } else { s += x; }
         if (rw[i].last) {
-          if (f) p.heads[(int64_t)c * p.ldh + rw[i].g] = s;
+          if (f) p.heads[(int64_t)c * p.ldh + rw[i].g] = s * __ldg(p.hrow + rw[i].g);
           else { open_g = rw[i].g; open_s = s; }
         }
       }
@@ -230,7 +231,10 @@ __global__ void __launch_bounds__(256, 3) k_leaf_agg(LeafParams p) {
         p.tflag[slot] = (uint8_t)f;
         p.tsum[slot] = s;
       }
-      if (open_g >= 0) p.heads[(int64_t)c * p.ldh + open_g] = se + open_s;
+      if (open_g >= 0) {
+        const double h = se + open_s;        // began in an earlier tile (fe == 0): k_heads_fix
+        p.heads[(int64_t)c * p.ldh + open_g] = fe ? h * __ldg(p.hrow + open_g) : h;
+      }
     }
   }
 }
@@ -301,10 +305,10 @@ __global__ void __launch_bounds__(256, 3) k_leaf_agg_mx(LeafParams p) {
         if (!rw[i].ok) continue;
         const dfl x = df_from_double(xs[i]);
         if (rw[i].pos == 0) { f = 1; s = x; } else { s = df_add(s, x); }
-        // group sums stored as the pair's bits (combined by heads_finish: a conversion here
-        // would be if-converted and issued for every element)
+        // the pair to float64 by integer instructions (df_to_double_int): a conversion on
+        // the FP64 pipe would be if-converted and issued for every element
         if (rw[i].last) {
-          if (f) p.heads[(int64_t)c * p.ldh + rw[i].g] = __hiloint2double(__float_as_int(s.hi), __float_as_int(s.lo));
+          if (f) p.heads[(int64_t)c * p.ldh + rw[i].g] = df_to_double_int(s.hi, s.lo) * __ldg(p.hrow + rw[i].g);
           else { open_g = rw[i].g; open_s = s; }
         }
       }
@@ -322,8 +326,9 @@ __global__ void __launch_bounds__(256, 3) k_leaf_agg_mx(LeafParams p) {
         p.tsum[slot] = df_to_double(s);
       }
       if (open_g >= 0) {
-        const dfl h = df_add(dfl{eh, el}, open_s);
-        p.heads[(int64_t)c * p.ldh + open_g] = __hiloint2double(__float_as_int(h.hi), __float_as_int(h.lo));
+        const dfl hs = df_add(dfl{eh, el}, open_s);
+        const double h = df_to_double_int(hs.hi, hs.lo);
+        p.heads[(int64_t)c * p.ldh + open_g] = fe ? h * __ldg(p.hrow + open_g) : h;
       }
     }
   }
@@ -387,45 +392,29 @@ static unsigned ht_grid(int64_t n_tiles) {
   return (unsigned)blocks;
 }
 
-// Head of every group: the partial sum written by the first pass (a float pair's bits on
-// the mixed path), plus the carry of the tile holding the group's last row when the group
-// began in an earlier tile, times 1 / sqrt(rows).  One thread per group walks the columns,
-// so the group's offsets and scale are read once.
-__global__ void k_heads_finish(LeafParams p, const int32_t* sizes, int mixed) {
-  const int64_t G = sizes[0];
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < G; g += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t t = ((int64_t)p.goff[g + 1] - 1) / kHtTile;
-    const bool carry = (int64_t)p.goff[g] < t * kHtTile;
-    const double hr = p.hrow[g];
-    // four columns at a time, every load before the first store (the stores may alias the
-    // loads as far as the compiler knows, which would otherwise serialise the columns)
-    for (int c0 = 0; c0 < p.N; c0 += 4) {
-      double s[4], cy[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int c = c0 + i;
-        s[i] = c < p.N ? p.heads[(int64_t)c * p.ldh + g] : 0.0;
-        cy[i] = (carry && c < p.N) ? p.tcarry[(int64_t)c * p.n_tiles + t] : 0.0;
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int c = c0 + i;
-        if (c >= p.N) break;
-        double v = s[i];
-        if (mixed) v = df_to_double_int(__int_as_float(__double2hiint(v)), __int_as_float(__double2loint(v)));
-        p.heads[(int64_t)c * p.ldh + g] = (v + cy[i]) * hr;
-      }
-    }
+// The head of the group that ends in tile t but began in an earlier tile (if any): its sum
+// from the tile start, written by the first pass, plus the tile's carry, times
+// 1 / sqrt(rows).  One thread per tile and column.
+__global__ void k_heads_fix(LeafParams p) {
+  const int64_t total = p.n_tiles * (int64_t)p.N;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = k / p.n_tiles, t = k - c * p.n_tiles;
+    const int64_t e = t * kHtTile;
+    const int32_t g = p.row_gid[e];
+    if ((int64_t)p.goff[g] >= e || (int64_t)p.goff[g + 1] - 1 >= e + kHtTile) continue;
+    double* h = p.heads + c * p.ldh + g;
+    *h = (*h + p.tcarry[k]) * p.hrow[g];
   }
 }
 
-void leaf_heads(const LeafParams& p, const int32_t* sizes, cudaStream_t st, int64_t* launches) {
+void leaf_heads(const LeafParams& p, cudaStream_t st, int64_t* launches) {
   if (p.N == 0) return;
   const unsigned g = ht_grid(p.n_tiles);
   if (p.mixed) k_leaf_agg_mx<<<g, 256, 0, st>>>(p);
   else k_leaf_agg<<<g, 256, 0, st>>>(p);
   k_tile_carry<<<p.N, kCarryThreads, 0, st>>>(p.tflag, p.tsum, p.tcarry, p.n_tiles, nullptr);
-  k_heads_finish<<<grid_for(p.M, 256, 152 * 8), 256, 0, st>>>(p, sizes, p.mixed);
+  k_heads_fix<<<grid_for(p.n_tiles * (int64_t)p.N, 256, 152 * 8), 256, 0, st>>>(p);
   *launches += 3;
 }
 

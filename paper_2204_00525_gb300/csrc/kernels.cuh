@@ -208,9 +208,9 @@ inline int row_pitch(int cols) { return (cols + 1) & ~1; }
 // copy out) against N sectors of 32 bytes for the plain gather, part of which hit L2 while
 // the table is not much larger than L2: they pay for tables of 1 GiB and more.
 inline bool row_gather_pays(int64_t rows, int cols) { return cols > 0 && (double)rows * cols * 8.0 >= 1073741824.0; }
-// Heads of a relation (first pass, tile carries, heads_finish) and, for tails blocks that
-// are materialised, the tails (last pass).
-void leaf_heads(const LeafParams& p, const int32_t* sizes, cudaStream_t st, int64_t* launches);
+// Heads of a relation (first pass, tile carries, the fix-up of groups that cross a tile
+// start) and, for tails blocks that are stored, the tails (last pass).
+void leaf_heads(const LeafParams& p, cudaStream_t st, int64_t* launches);
 void leaf_tails(const LeafParams& p, cudaStream_t st, int64_t* launches);
 void gen_heads_tails(const GenParams& p, cudaStream_t st, int64_t* launches);
 
