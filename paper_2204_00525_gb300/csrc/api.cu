@@ -151,6 +151,7 @@ struct figaro_batch_s {
   cudaGraphExec_t exec = nullptr;
   int* status_dev = nullptr;           // [n] every instance's error word, gathered
   int* status_host = nullptr;          // pinned copy
+  fig::JacobiTask* tasks_dev = nullptr; // the PCA instances' SVDs, one batched launch
   int64_t launches = 0;
 };
 
@@ -1326,6 +1327,7 @@ int figaro_batch_destroy(figaro_batch_t b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->status_dev) cudaFree(b->status_dev);
   if (b->status_host) cudaFreeHost(b->status_host);
+  if (b->tasks_dev) cudaFree(b->tasks_dev);
   if (b->st) cudaStreamDestroy(b->st);
   delete b;
   return FIGARO_OK;
@@ -1366,6 +1368,24 @@ int figaro_batch_create(int32_t n, const figaro_plan_t* plans, double* const* R,
     e = cudaMemcpy(words, w.data(), sizeof(int*) * n, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return bail(e, "batch setup");
   }
+  // the SVD + top-k components of every instance with k > 0: one thread block each, all in
+  // one launch after every instance's R
+  std::vector<JacobiTask> tasks;
+  int max_n = 0;
+  for (int i = 0; i < n; ++i) {
+    figaro_plan_s& P = *plans[i];
+    const int ki = k ? k[i] : 0;
+    if (ki <= 0) continue;
+    tasks.push_back(JacobiTask{P.Rtmp, P.N, P.N, P.svdW, P.svdV, P.sig, P.Vtmp, P.err_dev,
+                               P.opt.svd_max_sweeps > 0 ? P.opt.svd_max_sweeps : kSvdDefaultSweeps, components[i], eigvals[i], ki});
+    max_n = std::max(max_n, P.N);
+  }
+  if (!tasks.empty()) {
+    e = cudaMalloc(&B->tasks_dev, sizeof(JacobiTask) * tasks.size());
+    if (e == cudaSuccess)
+      e = cudaMemcpy(B->tasks_dev, tasks.data(), sizeof(JacobiTask) * tasks.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bail(e, "batch setup");
+  }
   // one capture: every plan's pipeline on its own streams, forked from and joined to the
   // batch stream, so the instances are independent branches of one graph
   cudaEvent_t fork = nullptr;
@@ -1383,13 +1403,6 @@ int figaro_batch_create(int32_t n, const figaro_plan_t* plans, double* const* R,
     e = cudaStreamWaitEvent(P.exec, fork, 0);
     if (e != cudaSuccess) break;
     rc = enqueue_r(P, P.Rtmp, P.N);
-    const int ki = k ? k[i] : 0;
-    if (rc == FIGARO_OK && ki > 0) {
-      jacobi_svd(P.Rtmp, P.N, P.N, P.svdW, P.svdV, P.sig, P.Vtmp, P.err_dev, P.exec, &B->launches, P.opt.svd_max_sweeps);
-      e = cudaMemcpy2DAsync(components[i], ki * sizeof(double), P.Vtmp, P.N * sizeof(double), ki * sizeof(double),
-                            P.N, cudaMemcpyDeviceToDevice, P.exec);
-      if (e == cudaSuccess) square_values(P.sig, eigvals[i], ki, P.exec, &B->launches);
-    }
     if (rc == FIGARO_OK && e == cudaSuccess)
       e = cudaMemcpyAsync(R[i], P.Rtmp, (size_t)P.N * P.N * sizeof(double), cudaMemcpyDeviceToDevice, P.exec);
     B->launches += P.launches;
@@ -1397,6 +1410,7 @@ int figaro_batch_create(int32_t n, const figaro_plan_t* plans, double* const* R,
     if (rc == FIGARO_OK && e == cudaSuccess) e = cudaStreamWaitEvent(B->st, P.join_out, 0);
   }
   if (e == cudaSuccess && rc == FIGARO_OK) {
+    jacobi_svd_batch(B->tasks_dev, (int)tasks.size(), max_n, B->st, &B->launches);
     k_gather_status<<<1, 256, 0, B->st>>>(words, n, B->status_dev);
     ++B->launches;
     e = cudaMemcpyAsync(B->status_host, B->status_dev, sizeof(int) * n, cudaMemcpyDeviceToHost, B->st);

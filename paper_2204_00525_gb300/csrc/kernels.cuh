@@ -268,8 +268,30 @@ double tsqr_leaf_flops(int64_t rows, int n);
 cudaError_t tsqr_set_attributes();
 
 // ------------------------------------------------------------------ svd.cu
-size_t jacobi_smem(int N);
+// One Jacobi SVD: R (row-major, ldr), work arrays W and V (N x N each, used when they do not
+// fit in shared memory), sigma[N] descending, Vout (row-major N x N), the error word, the
+// sweep limit; with k > 0 also the first k columns of Vout (comp, row-major N x k) and
+// sigma^2 (eig[k]).
+struct JacobiTask {
+  const double* R;
+  int64_t ldr;
+  int N;
+  double* W;
+  double* V;
+  double* sigma;
+  double* Vout;
+  int* err;
+  int max_sweeps;
+  double* comp;
+  double* eig;
+  int k;
+};
+constexpr size_t kJacobiSmemCap = 200 * 1024;
+constexpr int kSvdDefaultSweeps = 40;     // svd_max_sweeps = 0
+__host__ __device__ inline size_t jacobi_smem(int N) { return (2 * (size_t)N * N + N) * sizeof(double); }
 cudaError_t svd_set_attributes();
+// every task's SVD in one launch (one thread block each); max_n = the largest N
+void jacobi_svd_batch(const JacobiTask* tasks_dev, int n, int max_n, cudaStream_t st, int64_t* launches);
 void jacobi_svd(const double* R, int64_t ldr, int N, double* W, double* V, double* sigma,
                 double* Vout, int* err, cudaStream_t st, int64_t* launches, int max_sweeps);
 void square_values(const double* s, double* out, int k, cudaStream_t st, int64_t* launches);

@@ -8,64 +8,104 @@
 
 namespace fig {
 
-constexpr int kSvdThreads = 256;
-constexpr int kSvdMaxSweeps = 40;
+constexpr int kSvdThreads = 1024;   // 32 warps: one column pair per warp and round up to N = 64
+constexpr int kSvdMaxSweeps = kSvdDefaultSweeps;
+constexpr int kSvdMaxPairs = 512;      // N <= 1024 (the library's column limit)
 
-__global__ void __launch_bounds__(kSvdThreads) k_jacobi(const double* R, int64_t ldr, int N, double* Wg,
-                                                        double* Vg, double* sigma, double* Vout, int use_smem,
-                                                        int max_sweeps, int* err) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+// One SVD in one thread block: W = R (column j at W + j N), V = I; round-robin rounds of
+// disjoint column pairs until a sweep rotates no pair.  The block issues one FP64
+// instruction per warp every ~16 cycles at best, so a round is split into three phases
+// that keep the FP64 instruction count low: (1) one warp per pair forms w_p . w_q (the
+// squared column norms are carried: recomputed at every sweep start, updated exactly by
+// each rotation, |w_p'|^2 = |w_p|^2 - t g and |w_q'|^2 = |w_q|^2 + t g); (2) one thread per
+// pair forms the rotation (zeta = (|w_q|^2 - |w_p|^2) / 2g, t = sign(zeta) / (|zeta| +
+// sqrt(1 + zeta^2)), c = 1 / sqrt(1 + t^2), s = c t) instead of every lane of a warp;
+// (3) one warp per pair applies it to W and V.
+__device__ void jacobi_run(const JacobiTask& tk, double* smem, bool use_smem) {
   __shared__ int rotations;
-  double* W = use_smem ? reinterpret_cast<double*>(smem_raw) : Wg;   // column j at W + j N
-  double* V = use_smem ? W + (int64_t)N * N : Vg;
+  __shared__ double pg[kSvdMaxPairs];        // w_p . w_q of each pair of the round
+  __shared__ double2 pcs[kSvdMaxPairs];      // its rotation (c, s); c = 2 marks "no rotation"
+  const int N = tk.N;
+  double* W = use_smem ? smem : tk.W;
+  double* V = use_smem ? W + (int64_t)N * N : tk.V;
+  double* nrm = smem + (use_smem ? 2 * (int64_t)N * N : 0);   // squared column norms
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   for (int idx = tid; idx < N * N; idx += blockDim.x) {
     const int j = idx / N, i = idx - j * N;
-    W[idx] = R[(int64_t)i * ldr + j];
+    W[idx] = tk.R[(int64_t)i * tk.ldr + j];
     V[idx] = i == j ? 1.0 : 0.0;
   }
   __syncthreads();
   const int npad = N + (N & 1);
+  const int npairs = npad / 2;
+  // pair pi of round r: positions pi and npad-1-pi of the round-robin (circle) schedule,
+  // position 0 holding column 0 and position k >= 1 column 1 + (k - 1 + r) mod (npad - 1)
+  auto pair_of = [&](int pi, int r, int& p, int& q) {
+    const int pb = npad - 1 - pi;
+    const int a = pi == 0 ? 0 : 1 + (pi - 1 + r) % (npad - 1);
+    const int b = 1 + (pb - 1 + r) % (npad - 1);
+    p = a < b ? a : b;
+    q = a < b ? b : a;
+  };
   int sweep = 0;
-  for (; sweep < max_sweeps; ++sweep) {
+  for (; sweep < tk.max_sweeps; ++sweep) {
+    for (int j = warp; j < N; j += nw) {
+      double s2 = 0.0;
+      for (int i = lane; i < N; i += 32) s2 = fma(W[(int64_t)j * N + i], W[(int64_t)j * N + i], s2);
+      s2 = warp_sum(s2);
+      if (lane == 0) nrm[j] = s2;
+    }
     if (tid == 0) rotations = 0;
     __syncthreads();
     for (int r = 0; r < npad - 1; ++r) {
-      // round-robin (circle) schedule: position 0 holds player 0, position k >= 1
-      // holds player 1 + (k - 1 + r) mod (npad - 1); pair positions i and npad-1-i.
-      for (int pi = warp; pi < npad / 2; pi += nw) {
-        const int pa = pi, pb = npad - 1 - pi;
-        const int a = pa == 0 ? 0 : 1 + (pa - 1 + r) % (npad - 1);
-        const int b = 1 + (pb - 1 + r) % (npad - 1);
-        if (a >= N || b >= N) continue;
-        const int p = a < b ? a : b, q = a < b ? b : a;
+      for (int pi = warp; pi < npairs; pi += nw) {
+        int p, q;
+        pair_of(pi, r, p, q);
+        if (q >= N) continue;
+        const double* wp = W + (int64_t)p * N;
+        const double* wq = W + (int64_t)q * N;
+        double ga = 0.0;
+        for (int i = lane; i < N; i += 32) ga = fma(wp[i], wq[i], ga);
+        ga = warp_sum(ga);
+        if (lane == 0) pg[pi] = ga;
+      }
+      __syncthreads();
+      for (int pi = tid; pi < npairs; pi += blockDim.x) {
+        int p, q;
+        pair_of(pi, r, p, q);
+        double2 cs = make_double2(2.0, 0.0);
+        if (q < N) {
+          const double ga = pg[pi], al = nrm[p], be = nrm[q];
+          if (fabs(ga) > 1e-15 * sqrt(al * be) && fabs(ga) > 1e-300) {
+            const double zeta = (be - al) / (2.0 * ga);
+            const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            const double c = 1.0 / sqrt(1.0 + t * t);
+            cs = make_double2(c, c * t);
+            nrm[p] = al - t * ga;
+            nrm[q] = be + t * ga;
+            atomicAdd(&rotations, 1);
+          }
+        }
+        pcs[pi] = cs;
+      }
+      __syncthreads();
+      for (int pi = warp; pi < npairs; pi += nw) {
+        const double2 cs = pcs[pi];
+        if (cs.x > 1.5) continue;
+        int p, q;
+        pair_of(pi, r, p, q);
+        const double c = cs.x, s = cs.y;
         double* wp = W + (int64_t)p * N;
         double* wq = W + (int64_t)q * N;
-        double al = 0.0, be = 0.0, ga = 0.0;
+        double* vp = V + (int64_t)p * N;
+        double* vq = V + (int64_t)q * N;
         for (int i = lane; i < N; i += 32) {
           const double x = wp[i], y = wq[i];
-          al = fma(x, x, al);
-          be = fma(y, y, be);
-          ga = fma(x, y, ga);
-        }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
-        if (fabs(ga) > 1e-15 * sqrt(al * be) && fabs(ga) > 1e-300) {
-          const double zeta = (be - al) / (2.0 * ga);
-          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-          double* vp = V + (int64_t)p * N;
-          double* vq = V + (int64_t)q * N;
-          for (int i = lane; i < N; i += 32) {
-            const double x = wp[i], y = wq[i];
-            wp[i] = c * x - s * y;
-            wq[i] = s * x + c * y;
-            const double u = vp[i], w = vq[i];
-            vp[i] = c * u - s * w;
-            vq[i] = s * u + c * w;
-          }
-          if (lane == 0) atomicAdd(&rotations, 1);
+          wp[i] = c * x - s * y;
+          wq[i] = s * x + c * y;
+          const double u = vp[i], w = vq[i];
+          vp[i] = c * u - s * w;
+          vq[i] = s * u + c * w;
         }
       }
       __syncthreads();
@@ -74,9 +114,9 @@ __global__ void __launch_bounds__(kSvdThreads) k_jacobi(const double* R, int64_t
     __syncthreads();
     if (rot == 0) break;
   }
-  if (sweep == max_sweeps && tid == 0) set_error(err, FIGARO_ERR_TIMEOUT);
-  // sigma_j = ||W_j||, kept in the first row of the scratch after the loop
-  double* sig = reinterpret_cast<double*>(smem_raw) + (use_smem ? 2 * (int64_t)N * N : 0);
+  if (sweep == tk.max_sweeps && tid == 0) set_error(tk.err, FIGARO_ERR_TIMEOUT);
+  // sigma_j = ||W_j||, kept after W and V (or at the start of the shared buffer)
+  double* sig = smem + (use_smem ? 2 * (int64_t)N * N : 0);
   for (int j = warp; j < N; j += nw) {
     double s2 = 0.0;
     for (int i = lane; i < N; i += 32) s2 = fma(W[(int64_t)j * N + i], W[(int64_t)j * N + i], s2);
@@ -84,7 +124,8 @@ __global__ void __launch_bounds__(kSvdThreads) k_jacobi(const double* R, int64_t
     if (lane == 0) sig[j] = sqrt(s2);
   }
   __syncthreads();
-  // descending order, ties by index; every column signed so its largest entry is positive
+  // descending order, ties by index; every column signed so its largest entry is positive;
+  // with tk.k > 0 also the first k columns (PCA components, row-major N x k) and sigma^2
   for (int j = warp; j < N; j += nw) {
     const double sj = sig[j];
     int rank = 0;
@@ -105,28 +146,53 @@ __global__ void __launch_bounds__(kSvdThreads) k_jacobi(const double* R, int64_t
       if (ob > best || (ob == best && oa < arg)) { best = ob; arg = oa; }
     }
     const double sgn = vj[arg] < 0.0 ? -1.0 : 1.0;
-    if (lane == 0) sigma[rank] = sj;
-    for (int i = lane; i < N; i += 32) Vout[(int64_t)i * N + rank] = sgn * vj[i];
+    if (lane == 0) tk.sigma[rank] = sj;
+    for (int i = lane; i < N; i += 32) tk.Vout[(int64_t)i * N + rank] = sgn * vj[i];
+    if (rank < tk.k) {
+      if (lane == 0) tk.eig[rank] = sj * sj;
+      for (int i = lane; i < N; i += 32) tk.comp[(int64_t)i * tk.k + rank] = sgn * vj[i];
+    }
   }
+}
+
+__global__ void __launch_bounds__(kSvdThreads) k_jacobi(JacobiTask tk, int use_smem) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  jacobi_run(tk, reinterpret_cast<double*>(smem_raw), use_smem != 0);
+}
+
+// Many SVDs in one launch, one thread block per task; a task uses the shared buffer for W
+// and V when they fit in smem_bytes.
+__global__ void __launch_bounds__(kSvdThreads) k_jacobi_batch(const JacobiTask* tasks, size_t smem_bytes) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const JacobiTask tk = tasks[blockIdx.x];
+  jacobi_run(tk, reinterpret_cast<double*>(smem_raw), jacobi_smem(tk.N) <= smem_bytes);
 }
 
 __global__ void k_square(const double* s, double* out, int k) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) out[i] = s[i] * s[i];
 }
 
-size_t jacobi_smem(int N) { return (2 * (size_t)N * N + N) * sizeof(double); }
-
 cudaError_t svd_set_attributes() {
-  return cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, kJacobiSmemCap);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_jacobi_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, kJacobiSmemCap);
+  return e;
 }
 
 void jacobi_svd(const double* R, int64_t ldr, int N, double* W, double* V, double* sigma, double* Vout,
                 int* err, cudaStream_t st, int64_t* launches, int max_sweeps) {
+  JacobiTask tk{R, ldr, N, W, V, sigma, Vout, err, max_sweeps > 0 ? max_sweeps : kSvdMaxSweeps, nullptr, nullptr, 0};
   size_t smem = jacobi_smem(N);
-  const int use_smem = smem <= 200 * 1024;
+  const int use_smem = smem <= kJacobiSmemCap;
   if (!use_smem) smem = (size_t)N * sizeof(double);
-  k_jacobi<<<1, kSvdThreads, smem, st>>>(R, ldr, N, W, V, sigma, Vout, use_smem,
-                                        max_sweeps > 0 ? max_sweeps : kSvdMaxSweeps, err);
+  k_jacobi<<<1, kSvdThreads, smem, st>>>(tk, use_smem);
+  ++*launches;
+}
+
+void jacobi_svd_batch(const JacobiTask* tasks_dev, int n, int max_n, cudaStream_t st, int64_t* launches) {
+  if (n <= 0) return;
+  size_t smem = jacobi_smem(max_n);
+  if (smem > kJacobiSmemCap) smem = kJacobiSmemCap;
+  k_jacobi_batch<<<n, kSvdThreads, smem, st>>>(tasks_dev, smem);
   ++*launches;
 }
 
@@ -265,7 +331,8 @@ extern "C" int figaro_svd_from_r_static(const double* R, int64_t ldr, int32_t n,
   if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess)
     return record_error(FIGARO_ERR_CUDA, "figaro_svd_from_r_static: clearing the error word failed");
   const size_t smem = (size_t)n * sizeof(double);
-  k_jacobi<<<1, kSvdThreads, smem, st>>>(R, ldr, n, W, Vw, sigma, V, 0, kSvdMaxSweeps, err);
+  const JacobiTask tk{R, ldr, n, W, Vw, sigma, V, err, kSvdMaxSweeps, nullptr, nullptr, 0};
+  k_jacobi<<<1, kSvdThreads, smem, st>>>(tk, 0);
   cudaError_t le = cudaGetLastError();
   if (le != cudaSuccess)
     return record_error(FIGARO_ERR_CUDA, cudaGetErrorString(le));
