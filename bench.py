@@ -197,7 +197,8 @@ def run_plan_only(args):
     dev_inputs = make_inputs(db, torch, "cuda")
     prec = binding.FIGARO_PREC_MIXED if args.plan_only.startswith("mixed") else binding.FIGARO_PREC_FP64
     p = binding.JoinPlan(dev_inputs, db.parent, precision=prec, stage_timing=args.plan_only.endswith("staged"),
-                         stream=torch.cuda.current_stream(), fuse_tails=args.fuse_tails)
+                         stream=torch.cuda.current_stream(), fuse_tails=args.fuse_tails,
+                         autotune=args.autotune)
     p._R = torch.empty(db.n_cols, db.n_cols, dtype=torch.float64, device="cuda")
     ms = time_steps(p, torch, args.steps, args.warmup, lambda: None)
     p.close()
@@ -271,7 +272,9 @@ def run_batch(args):
     t0 = time.time()
     dbs = [synth.batch_instance(i) for i in range(args.batch_instances)]
     cells = sum(db.input_cells() for db in dbs)
-    plans = [binding.plan_from_db(db) for db in dbs]
+    t1 = time.time()
+    plans = [binding.plan_from_db(db, autotune=args.autotune) for db in dbs]
+    plan_s = time.time() - t1
     ks = [min(10, db.n_cols) for db in dbs]
     log(f"batch: {len(dbs)} instances, {cells / 1e6:.1f}M cells, setup {time.time() - t0:.1f}s")
     for _ in range(args.warmup):                      # one call each: graphs captured
@@ -295,6 +298,7 @@ def run_batch(args):
            "value": len(dbs) / (batch_ms * 1e-3), "unit": "instances/s", "ms_per_batch": batch_ms,
            "cells_per_s": cells / (batch_ms * 1e-3), "loop_ms": loop_ms, "speedup_vs_loop": loop_ms / batch_ms,
            "launches_per_batch": bt.launches(), "instances": len(dbs), "input_cells": cells,
+           "autotune": bool(args.autotune), "plans_s": plan_s,
            "steps": args.steps, "warmup": args.warmup, "dtype": "f64", "data": "synthetic (seeded)",
            "timing": "host clock around figaro_batch_run (launch + wait) / around the loop of "
                      "figaro_qr_r + figaro_pca calls (each waits)"}
@@ -733,6 +737,8 @@ def main():
                     help="--impl reference: rows of the workload divided by this")
     ap.add_argument("--plan-only", choices=["fp64", "mixed", "fp64-staged", "mixed-staged"],
                     help="profiling aid: run one plan only and print no JSON line")
+    ap.add_argument("--autotune", action="store_true",
+                    help="--plan-only / --batch-instances: TSQR plans picked by the autotuner (options.autotune)")
     ap.add_argument("--fuse-tails", action="store_true",
                     help="--plan-only: tails of relations with <= 32 columns formed inside the TSQR leaf")
     ap.add_argument("--workload", choices=["path3", "star", "snowflake", "snowflake-small"], default="snowflake",

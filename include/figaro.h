@@ -140,7 +140,16 @@ typedef struct figaro_join_tree {
  *                    FIGARO_PREC_MIXED_REFINED plans, nor under FIGARO_LEAF_GIVENS for
  *                    blocks of <= 16 columns); the same R up to rounding, less device
  *                    memory, about as fast (both halves are bound by arithmetic issue, not
- *                    by memory bandwidth).  Any other value: INVALID_ARG.              */
+ *                    by memory bandwidth).  Any other value: INVALID_ARG.
+ *   autotune         0 (default): every TSQR block's leaf tiles, chunk heights, blocks per
+ *                    SM, chunks per leaf triangle and tree fan follow the planner's rules
+ *                    (width, precision, shared-memory budget).  1: figaro_plan times a few
+ *                    candidate plans per block (the rule's among them) on synthetic rows
+ *                    of the block's width and row bound (at most 2^30 cells) and keeps the
+ *                    fastest; results are cached per (precision, leaf, width, row bucket)
+ *                    for the process, so equal shapes are tuned once.  The same R up to
+ *                    rounding (the float path keeps its bound of 16 chunks per leaf
+ *                    triangle).  Any other value: INVALID_ARG.                        */
 typedef struct figaro_options {
   int32_t precision;
   int32_t presorted;
@@ -152,7 +161,8 @@ typedef struct figaro_options {
   int32_t workspace_limit_mib;
   int32_t svd_max_sweeps;
   int32_t fuse_tails;
-  int32_t reserved[6];
+  int32_t autotune;
+  int32_t reserved[5];
 } figaro_options;
 
 typedef struct figaro_plan_s* figaro_plan_t;

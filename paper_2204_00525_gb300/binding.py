@@ -45,7 +45,7 @@ class figaro_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("presorted", C.c_int32), ("require_reduced", C.c_int32),
                 ("mem", C.c_int32), ("stage_timing", C.c_int32), ("gradients", C.c_int32),
                 ("leaf", C.c_int32), ("workspace_limit_mib", C.c_int32), ("svd_max_sweeps", C.c_int32),
-                ("fuse_tails", C.c_int32), ("reserved", C.c_int32 * 6)]
+                ("fuse_tails", C.c_int32), ("autotune", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class figaro_plan_info(C.Structure):
@@ -224,7 +224,7 @@ class JoinPlan:
     def __init__(self, relations, parent, precision=FIGARO_PREC_FP64, presorted=False,
                  require_reduced=False, mem=FIGARO_MEM_DEVICE, stage_timing=False, stream=None,
                  gradients=False, leaf=FIGARO_LEAF_HOUSEHOLDER, workspace_limit_mib=0, svd_max_sweeps=0,
-                 fuse_tails=False):
+                 fuse_tails=False, autotune=False):
         import torch
         self._keep = []
         self._data = []
@@ -264,6 +264,7 @@ class JoinPlan:
         opt.workspace_limit_mib = int(workspace_limit_mib)
         opt.svd_max_sweeps = int(svd_max_sweeps)
         opt.fuse_tails = int(fuse_tails)
+        opt.autotune = int(autotune)
         self.mem = mem
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.handle = figaro_plan(tree, opt, self.stream.cuda_stream)

@@ -549,6 +549,15 @@ static void make_links(figaro_plan_s& P) {
 
 static void make_blocks(figaro_plan_s& P) {
   const bool mixed = P.opt.precision != FIGARO_PREC_FP64;
+  const bool givens = P.opt.leaf == FIGARO_LEAF_GIVENS, tc5 = P.opt.leaf != FIGARO_LEAF_MMA_SYNC;
+  // the planner's rule, or the autotuner's fastest candidate (options.autotune)
+  auto plan_block = [&](TsqrBlock& t) {
+    tsqr_plan_block(t, mixed, givens, tc5);
+    if (P.opt.autotune && !t.fused) {
+      const TsqrTune tune = tsqr_autotune(t, mixed, givens, tc5);
+      tsqr_plan_block(t, mixed, givens, tc5, &tune);
+    }
+  };
   P.blocks.clear();
   P.stack_rows = 0;
   for (auto& n : P.nodes) {
@@ -562,7 +571,7 @@ static void make_blocks(figaro_plan_s& P) {
       t.bound = n.M;
       // formed inside the leaf where tsqr_plan_block allows it (<= 32 columns, Householder)
       t.fused = P.opt.precision != FIGARO_PREC_MIXED_REFINED && P.opt.fuse_tails;
-      tsqr_plan_block(t, mixed, P.opt.leaf == FIGARO_LEAF_GIVENS, P.opt.leaf != FIGARO_LEAF_MMA_SYNC);
+      plan_block(t);
       P.blocks.push_back(t);
       P.stack_rows += t.n;
     }
@@ -574,7 +583,7 @@ static void make_blocks(figaro_plan_s& P) {
       t.prio = true;
       t.M = n.M;
       t.bound = n.M;
-      tsqr_plan_block(t, mixed, P.opt.leaf == FIGARO_LEAF_GIVENS, P.opt.leaf != FIGARO_LEAF_MMA_SYNC);
+      plan_block(t);
       P.blocks.push_back(t);
       P.stack_rows += t.n;
     }
@@ -586,7 +595,7 @@ static void make_blocks(figaro_plan_s& P) {
       t.prio = true;
       t.M = n.M;
       t.bound = n.M;
-      tsqr_plan_block(t, mixed, P.opt.leaf == FIGARO_LEAF_GIVENS, P.opt.leaf != FIGARO_LEAF_MMA_SYNC);
+      plan_block(t);
       P.blocks.push_back(t);
       P.stack_rows += t.n;
     }
@@ -1111,6 +1120,10 @@ int figaro_plan(const figaro_join_tree* tree, const figaro_options* opt, void* s
   if (P->opt.mem != FIGARO_MEM_DEVICE && P->opt.mem != FIGARO_MEM_HOST) {
     delete P;
     return fail(FIGARO_ERR_INVALID_ARG, "mem");
+  }
+  if (P->opt.autotune != 0 && P->opt.autotune != 1) {
+    delete P;
+    return fail(FIGARO_ERR_INVALID_ARG, "autotune");
   }
   if (P->opt.fuse_tails != 0 && P->opt.fuse_tails != 1) {
     delete P;

@@ -246,6 +246,15 @@ struct TsqrBlock {
   bool fold_tc5;             // fold path, float leaf on tcgen05 (k_tsqr_fold_tc, 128-row chunks)
   int* err;                  // the plan's device error word (bounded waits report TIMEOUT)
   bool fused;                // tails block formed inside its leaf kernel (tails_qr): rows = M sorted rows
+  int fold_res;              // fold path: most thread blocks of a launch (T slots when T is global)
+};
+
+// A TSQR plan override chosen by the autotuner; 0 keeps the planner's rule for that field.
+struct TsqrTune {
+  int fold_budget_kib;       // fold path: shared memory of a thread block (chunk height, blocks per SM)
+  int seg_cap;               // fold path: at most this many chunks folded into one leaf triangle
+  int fan;                   // tree levels: triangles reduced per unit
+  int64_t warp_min;          // register path: levels with at least this many tiles take the warp kernel
 };
 
 // tsqr_tc.cu: the float leaf on the 5th-generation tensor cores
@@ -254,7 +263,12 @@ bool fold_tc_fits(int n);
 void launch_fold_tc(const TsqrBlock& b, double* tri_out, int* err, cudaStream_t st);
 cudaError_t fold_tc_set_attributes();
 
-void tsqr_plan_block(TsqrBlock& b, bool mixed, bool givens = false, bool tcgen05 = false);
+void tsqr_plan_block(TsqrBlock& b, bool mixed, bool givens = false, bool tcgen05 = false,
+                     const TsqrTune* tune = nullptr);
+// The fastest of the candidate plans of block b (its width, kind and row bound) measured on
+// synthetic rows (at most 2^30 cells) at plan time; results are kept per (precision, leaf,
+// width, row bucket) for the process.  Returns the override (zero: the rule's plan won).
+TsqrTune tsqr_autotune(const TsqrBlock& b, bool mixed, bool givens, bool tcgen05);
 // tails_qr_f64.cu: the tails of a relation with <= 32 data columns formed in registers and
 // triangularised by the leaf (the block's tri[0]), after leaf_heads has made the carries
 void tails_qr(const LeafParams& p, const TsqrBlock& b, cudaStream_t st, int64_t* launches);

@@ -870,7 +870,7 @@ template <typename E>
 static void launch_fold(const TsqrBlock& b, const double* tri_in, double* tri_out, int level, bool mixed,
                         cudaStream_t st) {
   int64_t grid = fold_units(b, level);
-  const int64_t cap = fold_resident(mixed);
+  const int64_t cap = b.fold_res > 0 ? b.fold_res : fold_resident(mixed);
   if (grid > cap) grid = cap;
   k_tsqr_fold<E><<<(unsigned)grid, kFoldThreads, fold_smem(b, sizeof(E)), st>>>(b, tri_in, tri_out, level);
 }
@@ -995,10 +995,12 @@ static size_t cta_smem(int lda, int n, size_t esz) { return (kRedElems + (size_t
 // triangle in shared memory when it takes at most a quarter of it, else in a global slot
 // per thread block), one leaf triangle per resident thread block (at most 16 chunks each on
 // the float path, whose error grows with the number of folds into one triangle).
-static bool fold_plan(TsqrBlock& b, bool mixed, size_t esz, bool tcgen05) {
+static bool fold_plan(TsqrBlock& b, bool mixed, size_t esz, bool tcgen05, const TsqrTune* tn) {
   const int n = b.n;
   if (n > kFoldWorkers) return false;          // T rows are staged one element per worker thread
-  const size_t budget = fold_budget(mixed);
+  size_t budget = fold_budget(mixed);
+  if (tn && tn->fold_budget_kib > 0 && (size_t)tn->fold_budget_kib * 1024 < budget)
+    budget = (size_t)tn->fold_budget_kib * 1024;
   const bool tc = mixed;                      // float leaf: tensor-core panels
   const size_t red = ((size_t)fold_red_elems(n) + (tc ? (size_t)fold_tc_extra(n) : 0)) * esz;
   if (red >= budget) return false;
@@ -1026,10 +1028,16 @@ static bool fold_plan(TsqrBlock& b, bool mixed, size_t esz, bool tcgen05) {
   // chunk as one chunk stacks, so one chunk per unit and level: fan = stack + 1 (2..16)
   const int64_t stack = mc / n;
   b.fan = (int)(stack + 1 < 2 ? 2 : (stack + 1 > 16 ? 16 : stack + 1));
+  if (tn && tn->fan >= 2) b.fan = tn->fan;
   const int64_t chunks = (b.bound + mc - 1) / mc;
-  const int64_t res = b.fold_tc5 ? 152 : fold_resident(mixed);
+  // thread blocks resident at once: one per SM for the tcgen05 leaf, else as many as the
+  // budget leaves room for (its tree levels keep the float fold's two per SM)
+  int64_t res = b.fold_tc5 ? 152 : fold_resident(mixed);
+  if (!b.fold_tc5 && tn && tn->fold_budget_kib > 0) res = 152 * (int64_t)(kSmemCap / budget);
+  b.fold_res = (int)(b.fold_tc5 ? fold_resident(true) : res);
   int64_t seg = (chunks + res - 1) / res;
-  if (mixed && seg > 16) seg = 16;
+  if (mixed && seg > 16) seg = 16;             // the float path's error grows with the folds per triangle
+  if (tn && tn->seg_cap > 0 && seg > tn->seg_cap) seg = tn->seg_cap;
   b.seg = seg < 1 ? 1 : seg;
   int64_t u = (chunks + b.seg - 1) / b.seg;
   b.fold_g0 = u < res ? u : res;
@@ -1043,7 +1051,7 @@ static bool fold_plan(TsqrBlock& b, bool mixed, size_t esz, bool tcgen05) {
   return true;
 }
 
-void tsqr_plan_block(TsqrBlock& b, bool mixed, bool givens, bool tcgen05) {
+void tsqr_plan_block(TsqrBlock& b, bool mixed, bool givens, bool tcgen05, const TsqrTune* tune) {
   const int n = b.n;
   const size_t esz = mixed ? sizeof(float) : sizeof(double);
   b.nreg = reg_class(n);
@@ -1058,10 +1066,12 @@ void tsqr_plan_block(TsqrBlock& b, bool mixed, bool givens, bool tcgen05) {
     // n <= 16: tree tiles fill a register tile (fan = TW / n >= 4); wider blocks reduce
     // their trees with the block-per-tile kernel only, six triangles at a time
     b.fan = b.nreg <= 16 ? b.tile / n : 6;
+    if (tune && tune->warp_min > 0) b.warp_min = tune->warp_min;
+    if (tune && tune->fan >= 2 && (b.nreg > 16 || tune->fan * n <= b.tile)) b.fan = tune->fan;
     if (b.givens) b.tile = kGivensRows;       // leaf chunks of the Givens leaf
     // tails formed in the leaf (tails_qr): QR tiles of 32 lanes x 8, 4 or 2 sorted rows
     else if (b.fused) b.tile = 32 * (b.nreg <= 8 ? 8 : b.nreg <= 16 ? 4 : 2);
-  } else if (fold_plan(b, mixed, esz, tcgen05)) {
+  } else if (fold_plan(b, mixed, esz, tcgen05, tune)) {
     return;
   } else {
     b.warp_min = 0;
@@ -1095,7 +1105,8 @@ int64_t tsqr_tri_elems(const TsqrBlock& b) {
 
 int64_t tsqr_scratch_elems(const TsqrBlock& b, bool mixed) {
   if (b.nreg) return 0;
-  if (b.fold) return b.fold_tsmem ? 0 : fold_resident(mixed) * b.n * b.n;   // T slots (as doubles: room for floats)
+  if (b.fold)                                  // T slots (as doubles: room for floats)
+    return b.fold_tsmem ? 0 : (b.fold_res > 0 ? b.fold_res : fold_resident(mixed)) * (int64_t)b.n * b.n;
   const size_t esz = mixed ? sizeof(float) : sizeof(double);
   int64_t need = 0;
   const int64_t grid = 152 * 2;
