@@ -120,6 +120,7 @@ struct figaro_plan_s {
   double* Rtmp = nullptr;
   double* svdW = nullptr;
   double* svdV = nullptr;
+  double* svdAux = nullptr;             // the cluster Jacobi's scratch (wide R)
   double* sig = nullptr;
   double* Vtmp = nullptr;
   double* hostbuf_dev = nullptr;        // staging for host-memory outputs
@@ -297,6 +298,7 @@ static void layout(figaro_plan_s& P, Arena& a) {
   }
   P.svdW = a.take<double>(NN);
   P.svdV = a.take<double>(NN);
+  P.svdAux = a.take<double>(jacobi_aux_elems(P.N));
   P.sig = a.take<double>(P.N);
   P.Vtmp = a.take<double>(NN);
   P.hostbuf_dev = a.take<double>(NN + P.N);
@@ -1290,7 +1292,8 @@ static int run_svd(figaro_plan_s& P, double* R_out) {
   if (rc != FIGARO_OK) return rc;
   StageClock clk(P);
   clk.start(7);
-  jacobi_svd(P.Rtmp, P.N, P.N, P.svdW, P.svdV, P.sig, P.Vtmp, P.err_dev, P.st, &P.launches, P.opt.svd_max_sweeps);
+  jacobi_svd(P.Rtmp, P.N, P.N, P.svdW, P.svdV, P.sig, P.Vtmp, P.err_dev, P.st, &P.launches, P.opt.svd_max_sweeps,
+             P.svdAux);
   clk.stop();
   if (R_out) {
     const bool host = P.opt.mem == FIGARO_MEM_HOST;
@@ -1520,7 +1523,8 @@ int figaro_project(figaro_plan_t p, int32_t mode, const double* R, int64_t ldr, 
     if (mode == FIGARO_PROJ_Q) {
       tri_inverse(R, ldr, N, P.scatter, P.err_dev, st);
     } else {
-      jacobi_svd(R, ldr, N, P.svdW, P.svdV, P.sig, P.Vtmp, P.err_dev, st, &P.launches, P.opt.svd_max_sweeps);
+      jacobi_svd(R, ldr, N, P.svdW, P.svdV, P.sig, P.Vtmp, P.err_dev, st, &P.launches, P.opt.svd_max_sweeps,
+                 P.svdAux);
       scale_v(P.Vtmp, P.sig, N, k, mode == FIGARO_PROJ_U, P.scatter, P.err_dev, st);
     }
     Xd = P.scatter;
@@ -1592,7 +1596,8 @@ int figaro_pca_centered(figaro_plan_t p, int32_t k, double* components, double* 
     join_colsum(n.b.heads, n.M, n.b.goff, n.b.hrow, n.b.phic, n.b.sizes, n.N, P.colsum + n.col_off, st, &P.launches);
   join_size(P.nodes[P.root].b.full, P.nodes[P.root].b.sizes, P.jsize, st, &P.launches);
   center_gram(P.Rtmp, P.N, P.colsum, P.jsize, P.scatter, st, &P.launches);
-  jacobi_svd(P.scatter, P.N, P.N, P.svdW, P.svdV, P.sig, P.Vtmp, P.err_dev, st, &P.launches, P.opt.svd_max_sweeps);
+  jacobi_svd(P.scatter, P.N, P.N, P.svdW, P.svdV, P.sig, P.Vtmp, P.err_dev, st, &P.launches, P.opt.svd_max_sweeps,
+             P.svdAux);
   const bool host = P.opt.mem == FIGARO_MEM_HOST;
   const cudaMemcpyKind kind = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   FIG_CUDA(cudaMemcpy2DAsync(components, k * sizeof(double), P.Vtmp, P.N * sizeof(double), k * sizeof(double), P.N,

@@ -306,8 +306,12 @@ __host__ __device__ inline size_t jacobi_smem(int N) { return (2 * (size_t)N * N
 cudaError_t svd_set_attributes();
 // every task's SVD in one launch (one thread block each); max_n = the largest N
 void jacobi_svd_batch(const JacobiTask* tasks_dev, int n, int max_n, cudaStream_t st, int64_t* launches);
+// aux (jacobi_aux_elems doubles, or null): the scratch of the cluster version used for R
+// too wide for one block's shared memory
 void jacobi_svd(const double* R, int64_t ldr, int N, double* W, double* V, double* sigma,
-                double* Vout, int* err, cudaStream_t st, int64_t* launches, int max_sweeps);
+                double* Vout, int* err, cudaStream_t st, int64_t* launches, int max_sweeps,
+                double* aux = nullptr);
+inline int64_t jacobi_aux_elems(int N) { return 3 * 512 + N + 2; }
 void square_values(const double* s, double* out, int k, cudaStream_t st, int64_t* launches);
 
 // figaro_last_error's message for entry points outside api.cu: record_error sets it and

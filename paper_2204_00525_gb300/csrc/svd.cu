@@ -4,13 +4,67 @@
 // sigma_j = ||W_j|| and V accumulates the rotations.  The paper used LAPACK's
 // divide and conquer on the CPU; one-sided Jacobi is chosen here for its high relative
 // accuracy and because every pair of a round-robin round can be rotated in parallel.
+#include <cooperative_groups.h>
+
 #include "kernels.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace fig {
 
 constexpr int kSvdThreads = 1024;   // 32 warps: one column pair per warp and round up to N = 64
 constexpr int kSvdMaxSweeps = kSvdDefaultSweeps;
 constexpr int kSvdMaxPairs = 512;      // N <= 1024 (the library's column limit)
+
+// sigma_j = ||W_j|| (into sig, N doubles of shared memory), sigma descending with ties by
+// index, every column of V signed so that its largest entry is positive; with tk.k > 0 also
+// the first k columns (PCA components, row-major N x k) and sigma^2.  One thread block.
+// With CG, W and V are read from L2 (__ldcg): other thread blocks of a cluster wrote them.
+template <bool CG = false>
+__device__ void jacobi_finish(const JacobiTask& tk, const double* W, const double* V, double* sig) {
+  auto ld = [](const double* a) { return CG ? __ldcg(a) : *a; };
+  const int N = tk.N;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int j = warp; j < N; j += nw) {
+    double s2 = 0.0;
+    for (int i = lane; i < N; i += 32) {
+      const double w = ld(W + (int64_t)j * N + i);
+      s2 = fma(w, w, s2);
+    }
+    s2 = warp_sum(s2);
+    if (lane == 0) sig[j] = sqrt(s2);
+  }
+  __syncthreads();
+  // descending order, ties by index; every column signed so its largest entry is positive;
+  // with tk.k > 0 also the first k columns (PCA components, row-major N x k) and sigma^2
+  for (int j = warp; j < N; j += nw) {
+    const double sj = sig[j];
+    int rank = 0;
+    for (int k = lane; k < N; k += 32) rank += (sig[k] > sj || (sig[k] == sj && k < j)) ? 1 : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o);
+    const double* vj = V + (int64_t)j * N;
+    double best = -1.0;
+    int arg = 0;
+    for (int i = lane; i < N; i += 32) {
+      const double a = fabs(ld(vj + i));
+      if (a > best) { best = a; arg = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oa = __shfl_xor_sync(0xffffffffu, arg, o);
+      if (ob > best || (ob == best && oa < arg)) { best = ob; arg = oa; }
+    }
+    const double sgn = ld(vj + arg) < 0.0 ? -1.0 : 1.0;
+    if (lane == 0) tk.sigma[rank] = sj;
+    for (int i = lane; i < N; i += 32) tk.Vout[(int64_t)i * N + rank] = sgn * ld(vj + i);
+    if (rank < tk.k) {
+      if (lane == 0) tk.eig[rank] = sj * sj;
+      for (int i = lane; i < N; i += 32) tk.comp[(int64_t)i * tk.k + rank] = sgn * ld(vj + i);
+    }
+  }
+}
 
 // One SVD in one thread block: W = R (column j at W + j N), V = I; round-robin rounds of
 // disjoint column pairs until a sweep rotates no pair.  The block issues one FP64
@@ -115,44 +169,7 @@ __device__ void jacobi_run(const JacobiTask& tk, double* smem, bool use_smem) {
     if (rot == 0) break;
   }
   if (sweep == tk.max_sweeps && tid == 0) set_error(tk.err, FIGARO_ERR_TIMEOUT);
-  // sigma_j = ||W_j||, kept after W and V (or at the start of the shared buffer)
-  double* sig = smem + (use_smem ? 2 * (int64_t)N * N : 0);
-  for (int j = warp; j < N; j += nw) {
-    double s2 = 0.0;
-    for (int i = lane; i < N; i += 32) s2 = fma(W[(int64_t)j * N + i], W[(int64_t)j * N + i], s2);
-    s2 = warp_sum(s2);
-    if (lane == 0) sig[j] = sqrt(s2);
-  }
-  __syncthreads();
-  // descending order, ties by index; every column signed so its largest entry is positive;
-  // with tk.k > 0 also the first k columns (PCA components, row-major N x k) and sigma^2
-  for (int j = warp; j < N; j += nw) {
-    const double sj = sig[j];
-    int rank = 0;
-    for (int k = lane; k < N; k += 32) rank += (sig[k] > sj || (sig[k] == sj && k < j)) ? 1 : 0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o);
-    const double* vj = V + (int64_t)j * N;
-    double best = -1.0;
-    int arg = 0;
-    for (int i = lane; i < N; i += 32) {
-      const double a = fabs(vj[i]);
-      if (a > best) { best = a; arg = i; }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oa = __shfl_xor_sync(0xffffffffu, arg, o);
-      if (ob > best || (ob == best && oa < arg)) { best = ob; arg = oa; }
-    }
-    const double sgn = vj[arg] < 0.0 ? -1.0 : 1.0;
-    if (lane == 0) tk.sigma[rank] = sj;
-    for (int i = lane; i < N; i += 32) tk.Vout[(int64_t)i * N + rank] = sgn * vj[i];
-    if (rank < tk.k) {
-      if (lane == 0) tk.eig[rank] = sj * sj;
-      for (int i = lane; i < N; i += 32) tk.comp[(int64_t)i * tk.k + rank] = sgn * vj[i];
-    }
-  }
+  jacobi_finish(tk, W, V, smem + (use_smem ? 2 * (int64_t)N * N : 0));
 }
 
 __global__ void __launch_bounds__(kSvdThreads) k_jacobi(JacobiTask tk, int use_smem) {
@@ -172,6 +189,120 @@ __global__ void k_square(const double* s, double* out, int k) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) out[i] = s[i] * s[i];
 }
 
+// One SVD on a cluster of kSvdCluster thread blocks (wide R: W and V do not fit in one
+// block's shared memory and live in L2, where one SM's FP64 rate would set the pace): the
+// same three-phase rounds, with the pairs, rotations and column norms spread over the
+// cluster's warps and threads, W, V and the round's scratch in global memory read through
+// L2 (__ldcg), and a cluster barrier (release/acquire) between the phases.  aux holds the
+// round's (c, s) and dot products, the column norms and two rotation counters.
+constexpr int kSvdCluster = 8;
+
+__global__ void __cluster_dims__(kSvdCluster, 1, 1) __launch_bounds__(kSvdThreads)
+    k_jacobi_cluster(JacobiTask tk, double* aux) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int N = tk.N;
+  const int npad = N + (N & 1), npairs = npad / 2;
+  double2* pcs = reinterpret_cast<double2*>(aux);            // [kSvdMaxPairs]
+  double* pg = aux + 2 * kSvdMaxPairs;                       // [kSvdMaxPairs]
+  double* nrm = aux + 3 * kSvdMaxPairs;                      // [N]
+  int* rotc = reinterpret_cast<int*>(aux + 3 * kSvdMaxPairs + N);   // two counters
+  double* W = tk.W;
+  double* V = tk.V;
+  const int lane = threadIdx.x & 31;
+  const int gt = (int)cluster.block_rank() * blockDim.x + threadIdx.x;
+  const int gthreads = kSvdCluster * blockDim.x;
+  const int gw = gt >> 5, nwg = gthreads >> 5;
+  for (int idx = gt; idx < N * N; idx += gthreads) {
+    const int j = idx / N, i = idx - j * N;
+    W[idx] = tk.R[(int64_t)i * tk.ldr + j];
+    V[idx] = i == j ? 1.0 : 0.0;
+  }
+  if (gt == 0) rotc[0] = rotc[1] = 0;
+  cluster.sync();
+  auto pair_of = [&](int pi, int r, int& p, int& q) {
+    const int pb = npad - 1 - pi;
+    const int a = pi == 0 ? 0 : 1 + (pi - 1 + r) % (npad - 1);
+    const int b = 1 + (pb - 1 + r) % (npad - 1);
+    p = a < b ? a : b;
+    q = a < b ? b : a;
+  };
+  int sweep = 0;
+  for (; sweep < tk.max_sweeps; ++sweep) {
+    for (int j = gw; j < N; j += nwg) {
+      double s2 = 0.0;
+      for (int i = lane; i < N; i += 32) {
+        const double w = __ldcg(W + (int64_t)j * N + i);
+        s2 = fma(w, w, s2);
+      }
+      s2 = warp_sum(s2);
+      if (lane == 0) nrm[j] = s2;
+    }
+    cluster.sync();
+    // the next sweep's counter: every thread block read it (at the end of the previous
+    // sweep) before it reached the barrier above; it is next counted after the next
+    // sweep's first barrier.  So every block takes the same break below.
+    if (gt == 0) rotc[(sweep + 1) & 1] = 0;
+    for (int r = 0; r < npad - 1; ++r) {
+      for (int pi = gw; pi < npairs; pi += nwg) {
+        int p, q;
+        pair_of(pi, r, p, q);
+        if (q >= N) continue;
+        const double* wp = W + (int64_t)p * N;
+        const double* wq = W + (int64_t)q * N;
+        double ga = 0.0;
+        for (int i = lane; i < N; i += 32) ga = fma(__ldcg(wp + i), __ldcg(wq + i), ga);
+        ga = warp_sum(ga);
+        if (lane == 0) pg[pi] = ga;
+      }
+      cluster.sync();
+      for (int pi = gt; pi < npairs; pi += gthreads) {
+        int p, q;
+        pair_of(pi, r, p, q);
+        double2 cs = make_double2(2.0, 0.0);
+        if (q < N) {
+          const double ga = __ldcg(pg + pi), al = __ldcg(nrm + p), be = __ldcg(nrm + q);
+          if (fabs(ga) > 1e-15 * sqrt(al * be) && fabs(ga) > 1e-300) {
+            const double zeta = (be - al) / (2.0 * ga);
+            const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            const double c = 1.0 / sqrt(1.0 + t * t);
+            cs = make_double2(c, c * t);
+            nrm[p] = al - t * ga;
+            nrm[q] = be + t * ga;
+            atomicAdd(rotc + (sweep & 1), 1);
+          }
+        }
+        pcs[pi] = cs;
+      }
+      cluster.sync();
+      for (int pi = gw; pi < npairs; pi += nwg) {
+        const double2 cs = __ldcg(pcs + pi);
+        if (cs.x > 1.5) continue;
+        int p, q;
+        pair_of(pi, r, p, q);
+        const double c = cs.x, s = cs.y;
+        double* wp = W + (int64_t)p * N;
+        double* wq = W + (int64_t)q * N;
+        double* vp = V + (int64_t)p * N;
+        double* vq = V + (int64_t)q * N;
+        for (int i = lane; i < N; i += 32) {
+          const double x = __ldcg(wp + i), y = __ldcg(wq + i);
+          wp[i] = c * x - s * y;
+          wq[i] = s * x + c * y;
+          const double u = __ldcg(vp + i), w = __ldcg(vq + i);
+          vp[i] = c * u - s * w;
+          vq[i] = s * u + c * w;
+        }
+      }
+      cluster.sync();
+    }
+    const int rot = __ldcg(rotc + (sweep & 1));
+    if (rot == 0) break;
+  }
+  if (sweep == tk.max_sweeps && gt == 0) set_error(tk.err, FIGARO_ERR_TIMEOUT);
+  if (cluster.block_rank() == 0) jacobi_finish<true>(tk, W, V, reinterpret_cast<double*>(smem_raw));
+}
+
 cudaError_t svd_set_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, kJacobiSmemCap);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_jacobi_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, kJacobiSmemCap);
@@ -179,10 +310,15 @@ cudaError_t svd_set_attributes() {
 }
 
 void jacobi_svd(const double* R, int64_t ldr, int N, double* W, double* V, double* sigma, double* Vout,
-                int* err, cudaStream_t st, int64_t* launches, int max_sweeps) {
+                int* err, cudaStream_t st, int64_t* launches, int max_sweeps, double* aux) {
   JacobiTask tk{R, ldr, N, W, V, sigma, Vout, err, max_sweeps > 0 ? max_sweeps : kSvdMaxSweeps, nullptr, nullptr, 0};
   size_t smem = jacobi_smem(N);
   const int use_smem = smem <= kJacobiSmemCap;
+  if (!use_smem && aux) {                      // wide R: one cluster of thread blocks
+    k_jacobi_cluster<<<kSvdCluster, kSvdThreads, (size_t)N * sizeof(double), st>>>(tk, aux);
+    ++*launches;
+    return;
+  }
   if (!use_smem) smem = (size_t)N * sizeof(double);
   k_jacobi<<<1, kSvdThreads, smem, st>>>(tk, use_smem);
   ++*launches;
