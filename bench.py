@@ -409,6 +409,32 @@ def staged_run(binding, torch, inputs, parent, stream, steps, warmup, barrier, *
     return p, ms, st, blocks
 
 
+def time_spectral(plan, torch, steps, warmup, stream, G_ref):
+    """figaro_svd (R and its Jacobi SVD) and figaro_pca (k = 10) per call with CUDA events on
+    the plan's stream; sigma against the square roots of the oracle's factorized A^T A."""
+    out = {}
+    for name, call in (("svd", lambda: plan.svd()), ("pca_k10", lambda: plan.pca(10))):
+        for _ in range(max(1, warmup)):
+            res = call()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            res = call()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name + "_ms_per_call"] = e0.elapsed_time(e1) / steps
+        if name == "svd":
+            sig = res[0].cpu().numpy()
+    if G_ref is not None:
+        lam = np.sort(np.linalg.eigvalsh(G_ref))[::-1]
+        ref = np.sqrt(np.maximum(lam, 0.0))
+        out["sigma_max_rel_err_vs_oracle_gram"] = float(np.max(np.abs(sig - ref)) / ref[0])
+        out["sigma_ref"] = "square roots of the eigenvalues of the stored oracle A^T A (tests/golden)"
+    out["includes"] = "R (as figaro_qr_r) and the Jacobi SVD of R; FP64"
+    return out
+
+
 def run_figaro(args):
     import torch
     from paper_2204_00525_gb300 import binding
@@ -444,6 +470,7 @@ def run_figaro(args):
     lat64 = max_over_ranks(time_steps(p64, torch, K, W, barrier))
     info = p64.info()
     R64 = p64._R.cpu().numpy()
+    svd_rec = time_spectral(p64, torch, K2, W, stream, G_ref)
     p64.close()
     pst, ms_st64, st64, blk64 = staged_run(binding, torch, dev, db.parent, stream, K2, W, barrier)
     roof64, sizes = stage_rooflines(pst, st64, db, hbm, fp64_rate, False)
@@ -595,6 +622,7 @@ def run_figaro(args):
         "blocks": [{"n": n, "rows": r, "leaf_ms": m} for m, n, r in blk64 if r > 0],
         "r0_rows": info["r0_rows"],
         "roofline": roofline,
+        "spectral": svd_rec,
         "backward": {"ms_per_call": bwd_ms, "loss": "||R||_F^2", "value": cells * world / (bwd_ms * 1e-3),
                      "unit": "cells/s", "note": "figaro_backward after a forward call (pre-sorted plan)"},
         "e2e": {"value": cells * world / (e2e_ms * 1e-3), "unit": "cells/s", "ms_per_step": e2e_ms,
