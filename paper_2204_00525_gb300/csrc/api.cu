@@ -252,6 +252,7 @@ static void layout(figaro_plan_s& P, Arena& a) {
     n.n_tiles = ht_tiles(M);
     const int wide = std::max(std::max(n.N, n.N_sub), 1);
     b.tflag = a.take<uint8_t>(n.n_tiles * wide);
+    b.ttail = a.take<uint8_t>(n.n_tiles);
     b.tsum = a.take<double>(n.n_tiles * wide);
     b.tcarry = a.take<double>(n.n_tiles * wide);
     b.ltcarry = a.take<double>(n.n_tiles * std::max(n.N, 1));
@@ -854,6 +855,7 @@ static int enqueue_r(figaro_plan_s& P, double* R, int64_t ldr) {
     lp.heads = n.b.heads;
     lp.ldh = n.M;
     lp.tflag = n.b.tflag;
+    lp.ttail = n.b.ttail;
     lp.tsum = n.b.tsum;
     lp.tcarry = n.b.ltcarry;
     // lane partials for the stored tails pass and for a fused leaf with the first pass's

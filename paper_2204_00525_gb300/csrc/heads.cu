@@ -184,6 +184,18 @@ __device__ __forceinline__ void store_lane_and_tile(int f, double s, int lane, i
   }
 }
 
+// Whether the tile holds a tail row (one after its group's first): a tile of single-row
+// groups (a key column with distinct values, as the key-fkey joins' dimension and fact
+// tables mostly are) has no tails, and the tails pass skips it without reading its data.
+__device__ __forceinline__ void mark_tail_tile(const LeafParams& p, const LeafRow (&rw)[kHtItems], int64_t t,
+                                               int lane) {
+  bool any = false;
+#pragma unroll
+  for (int i = 0; i < kHtItems; ++i) any = any || (rw[i].ok && rw[i].pos > 0);
+  any = __any_sync(0xffffffffu, any);
+  if (p.ttail && lane == 0) p.ttail[t] = any ? 1 : 0;
+}
+
 // Pass 1: per tile and column, the tile aggregate (for the carry scan), every lane's
 // exclusive (flag, sum) inside the tile when a tails pass follows (lflag set), and the head
 // of every group that begins in the tile (its sum times 1 / sqrt(rows)), so that the heads
@@ -201,6 +213,7 @@ __global__ void __launch_bounds__(256, 3) k_leaf_agg(LeafParams p) {
     LeafRow rw[kHtItems];
 #pragma unroll
     for (int i = 0; i < kHtItems; ++i) rw[i] = leaf_row(p, e0 + i);
+    mark_tail_tile(p, rw, t, lane);
     for (int c = 0; c < p.N; ++c) {
       double xs[kHtItems];
       load_leaf_items(p, rw, e0, c, p.sorted_ready != 0, xs);
@@ -247,6 +260,7 @@ __global__ void __launch_bounds__(256, 2) k_leaf_emit(LeafParams p) {
   const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t t = wid; t < p.n_tiles; t += nwarps) {
+    if (p.ttail && !p.ttail[t]) continue;   // single-row groups only: no tail to write
     const int64_t e0 = t * kHtTile + (int64_t)lane * kHtItems;
     LeafRow rw[kHtItems];
     double ca[kHtItems], cb[kHtItems];    // tail = ca x - cb S: ca = g p beta_p, cb = g beta_p
@@ -293,6 +307,7 @@ __global__ void __launch_bounds__(256, 3) k_leaf_agg_mx(LeafParams p) {
     LeafRow rw[kHtItems];
 #pragma unroll
     for (int i = 0; i < kHtItems; ++i) rw[i] = leaf_row(p, e0 + i);
+    mark_tail_tile(p, rw, t, lane);
     for (int c = 0; c < p.N; ++c) {
       double xs[kHtItems];
       load_leaf_items(p, rw, e0, c, p.sorted_ready != 0, xs);
@@ -342,6 +357,7 @@ __global__ void __launch_bounds__(256, LO ? 2 : 3) k_leaf_emit_mx(LeafParams p) 
   const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t t = wid; t < p.n_tiles; t += nwarps) {
+    if (p.ttail && !p.ttail[t]) continue;   // single-row groups only: no tail to write
     const int64_t e0 = t * kHtTile + (int64_t)lane * kHtItems;
     LeafRow rw[kHtItems];
     dfl gam[kHtItems];                    // sqrt(Phi_circ) beta_p (the low part only when refining)

@@ -59,6 +59,7 @@ struct NodeBuf {
   double* rootrows;     // [M x N] col-major (root only)
   // scan tile aggregates
   uint8_t* tflag;       // [n_tiles * max(N_i, N_sub)]
+  uint8_t* ttail;       // [n_tiles]: the relation pass's tile holds a tail row (a row after its group's first)
   double* tsum;
   double* tcarry;
   double* ltcarry;      // tile carries of the relation pass (a fused leaf reads them while the
@@ -160,6 +161,7 @@ struct LeafParams {
   double* tcarry;
   uint8_t* lflag;
   double* lsum;
+  uint8_t* ttail;            // per tile: 1 if it holds a tail row (set by the first pass); null: unknown
   int64_t n_tiles;
 };
 

@@ -82,6 +82,13 @@ __global__ void __launch_bounds__(kFusedThreads) k_tails_qr(LeafParams p, int n,
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t n_qr = (p.M + TW - 1) / TW;
   for (int64_t t = gw; t < p.n_tiles; t += nw) {
+    if (p.ttail && !p.ttail[t]) {          // single-row groups only: zero triangles
+      for (int s = 0; s < S && t * S + s < n_qr; ++s) {
+        double* tri = tri_out + (t * S + s) * n * n;
+        for (int i = lane; i < n * n; i += 32) tri[i] = 0.0;
+      }
+      continue;
+    }
 #pragma unroll 1
     for (int s = 0; s < S; ++s) {
       const int64_t q = t * S + s;
