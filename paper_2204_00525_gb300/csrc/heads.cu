@@ -472,6 +472,19 @@ __device__ __forceinline__ GenRow gen_row(const GenParams& p, int64_t e, int64_t
 // segments of 32 groups.
 constexpr int kGatherMaxCols = 1024;
 
+// x f as a float64, or (PAIRS) as a double-float product stored as the pair's bits
+template <bool PAIRS>
+__device__ __forceinline__ double scaled(double x, double f) {
+  if (!PAIRS) return x * f;
+  const dfl r = df_mul(df_from_double(x), df_from_double(f));
+  return __hiloint2double(__float_as_int(r.hi), __float_as_int(r.lo));
+}
+
+// PAIRS (the mixed path's joined Data): every value and factor is split into a float pair
+// (exactly enough, 2^-47, by integer instructions), the product formed in double-float on
+// the FP32 pipe and stored as the pair's bits in the float64 slot, so that neither this
+// kernel nor the two scans that read it issue FP64 instructions per value.
+template <bool PAIRS>
 __global__ void __launch_bounds__(256) k_gen_gather(GenParams p, double* J, int64_t ldj) {
   __shared__ double tile[32][33];
   __shared__ int2 cd[kGatherMaxCols];              // column descriptors (N <= 1024)
@@ -505,7 +518,7 @@ __global__ void __launch_bounds__(256) k_gen_gather(GenParams p, double* J, int6
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int c = c0 + 8 * u;
-        if (c < p.N && cd[c].x == 0 && g < G) J[(int64_t)c * ldj + g] = v[u] * fs[0][lane];
+        if (c < p.N && cd[c].x == 0 && g < G) J[(int64_t)c * ldj + g] = scaled<PAIRS>(v[u], fs[0][lane]);
       }
     }
     // children's rows: lanes over columns, the warp's four rows loaded before they are used
@@ -525,7 +538,7 @@ __global__ void __launch_bounds__(256) k_gen_gather(GenParams p, double* J, int6
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int r = warp + 8 * u;
-        tile[r][lane] = d.x > 0 ? v[u] * fs[d.x][r] : 0.0;
+        tile[r][lane] = d.x > 0 ? scaled<PAIRS>(v[u], fs[d.x][r]) : 0.0;
       }
       __syncthreads();
       for (int c2 = cc + warp; c2 < cc + 32 && c2 < p.N; c2 += 8)
@@ -549,6 +562,26 @@ __device__ __forceinline__ void load_joined(const GenParams& p, const GenRow (&r
   } else {
 #pragma unroll
     for (int i = 0; i < kHtItems; ++i) Ds[i] = rw[i].ok ? col[i] : 0.0;
+  }
+}
+
+// The same values of the mixed path's joined Data, stored as float pairs
+__device__ __forceinline__ void load_joined_pairs(const GenParams& p, const GenRow (&rw)[kHtItems], int64_t e0,
+                                                  int c, int64_t G, dfl (&Ds)[kHtItems]) {
+  const float2* col = reinterpret_cast<const float2*>(p.jdata + (int64_t)c * p.ldj + e0);
+  if (e0 + kHtItems <= G) {
+#pragma unroll
+    for (int i = 0; i < kHtItems; i += 2) {
+      const float4 v = *reinterpret_cast<const float4*>(col + i);
+      Ds[i] = dfl{v.y, v.x};                 // the hi float is the upper half of the slot
+      Ds[i + 1] = dfl{v.w, v.z};
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < kHtItems; ++i) {
+      const float2 v = rw[i].ok ? col[i] : make_float2(0.0f, 0.0f);
+      Ds[i] = dfl{v.y, v.x};
+    }
   }
 }
 
@@ -643,14 +676,14 @@ __global__ void __launch_bounds__(256) k_gen_agg_mx(GenParams p) {
       vv[i] = df_from_double(rw[i].v);
     }
     for (int c = 0; c < p.N; ++c) {
-      double Ds[kHtItems];
-      load_joined(p, rw, e0, c, G, Ds);
+      dfl Ds[kHtItems];
+      load_joined_pairs(p, rw, e0, c, G, Ds);
       int f = 0;
       dfl s{0.0f, 0.0f};
 #pragma unroll
       for (int i = 0; i < kHtItems; ++i) {
         if (!rw[i].ok) continue;
-        const dfl x = df_mul(vv[i], df_from_double(Ds[i]));
+        const dfl x = df_mul(vv[i], Ds[i]);
         if (rw[i].k == 0) { f = 1; s = x; } else { s = df_add(s, x); }
       }
       pair_scan_incl_df(f, s, lane);
@@ -692,13 +725,13 @@ __global__ void __launch_bounds__(256, 2) k_gen_emit_mx(GenParams p) {
       const int fe = p.lflag[slot * 32 + lane];
       const double se = p.lsum[slot * 32 + lane];
       dfl run = df_from_double(fe ? se : p.tcarry[slot] + se);
-      double Ds[kHtItems];
-      load_joined(p, rw, e0, c, G, Ds);
+      dfl Ds[kHtItems];
+      load_joined_pairs(p, rw, e0, c, G, Ds);
       float* tcol = p.gtails32 + (int64_t)c * p.M;
 #pragma unroll
       for (int i = 0; i < kHtItems; ++i) {
         if (!rw[i].ok) continue;
-        const dfl D = df_from_double(Ds[i]);
+        const dfl D = Ds[i];
         if (rw[i].k == 0) run = dfl{0.0f, 0.0f};
         if (rw[i].k > 0) {
           const dfl d = df_add(df_mul(ww[i], D), df_neg(df_mul(vv[i], run)));
@@ -732,11 +765,12 @@ static unsigned gather_grid(int64_t rows) {
 
 void gen_heads_tails(const GenParams& p, cudaStream_t st, int64_t* launches) {
   if (p.is_root) {          // Out.append(Data): the joined Data is the root block itself
-    k_gen_gather<<<gather_grid(p.M), 256, 0, st>>>(p, p.rootrows, p.M);
+    k_gen_gather<false><<<gather_grid(p.M), 256, 0, st>>>(p, p.rootrows, p.M);
     ++*launches;
     return;
   }
-  k_gen_gather<<<gather_grid(p.M), 256, 0, st>>>(p, const_cast<double*>(p.jdata), p.ldj);
+  if (p.gtails32) k_gen_gather<true><<<gather_grid(p.M), 256, 0, st>>>(p, const_cast<double*>(p.jdata), p.ldj);
+  else k_gen_gather<false><<<gather_grid(p.M), 256, 0, st>>>(p, const_cast<double*>(p.jdata), p.ldj);
   const unsigned g = ht_grid(p.n_tiles);
   if (p.gtails32) k_gen_agg_mx<<<g, 256, 0, st>>>(p);
   else k_gen_agg<<<g, 256, 0, st>>>(p);

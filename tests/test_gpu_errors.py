@@ -79,3 +79,30 @@ def test_jacobi_sweep_limit_gives_timeout_and_plan_survives():
     s, _ = q.svd()
     assert np.allclose(s.cpu().numpy(), np.linalg.svd(R, compute_uv=False), rtol=0, atol=1e-10 * np.linalg.norm(R))
     q.close()
+
+
+def test_wide_svd_cluster_path_and_timeout():
+    """Above ~110 columns the Jacobi SVD runs on a cluster of thread blocks: its singular
+    values and vectors match LAPACK on the same R, and a sweep limit of 1 ends every block
+    of the cluster with FIGARO_ERR_TIMEOUT (one shared exit decision), the plan usable."""
+    from paper_2204_00525_gb300 import binding
+    binding.load(build_if_missing=True)
+    db = synth.two_relation(seed=91, rows=20_000, keys=300, n_s=70, n_t=60)   # N = 130
+    p = binding.plan_from_db(db)
+    s, V, R = p.svd(with_r=True)
+    R = R.cpu().numpy()
+    U_ref, s_ref, Vt_ref = np.linalg.svd(R)
+    assert np.allclose(s.cpu().numpy(), s_ref, rtol=0, atol=1e-12 * s_ref[0])
+    V = V.cpu().numpy()
+    for j in range(8):                         # the leading vectors, up to sign
+        assert abs(abs(V[:, j] @ Vt_ref[j]) - 1.0) < 1e-9
+    p.close()
+    q = binding.plan_from_db(db, svd_max_sweeps=1)
+    with pytest.raises(binding.FigaroError) as e:
+        q.svd()
+    assert e.value.status == binding.FIGARO_ERR_TIMEOUT
+    q.close()
+    r = binding.plan_from_db(db)                  # a fresh plan after the timed-out one
+    s2, _ = r.svd()
+    assert np.allclose(s2.cpu().numpy(), s_ref, rtol=0, atol=1e-12 * s_ref[0])
+    r.close()
