@@ -205,6 +205,42 @@ def run_plan_only(args):
     log(f"{args.plan_only}: {ms:.3f} ms per step")
 
 
+# FiGaRo-MKL seconds for R on the Cartesian product S x T (paper's Exp. 1 grid, its own
+# 24-core Xeon Silver 4214 machine): rows per relation -> {columns per relation: seconds}
+PAPER_CARTESIAN_S = {512: {64: 0.10, 256: 0.13}, 1024: {64: 0.10, 256: 0.13}, 2048: {64: 0.12, 256: 0.15},
+                     4096: {64: 0.12, 256: 0.14}, 8192: {64: 0.13, 256: 0.18}}
+
+
+def run_cartesian(args):
+    """--cartesian: R of the Cartesian product S x T with U[-3,3) data over the paper's
+    Exp. 1 grid (2^9..2^13 rows and 2^6, 2^8 columns per relation; 2^10 and 2^12 columns
+    per relation exceed this library's 1024 columns of R), FP64 and mixed, one call at a
+    time with CUDA events, beside the paper's FiGaRo-MKL times on its own CPU machine
+    (context, not a target: other hardware).  Prints one JSON line."""
+    import torch
+    from paper_2204_00525_gb300 import binding
+    binding.load(build_if_missing=True)
+    stream = torch.cuda.current_stream()
+    rows = []
+    for m in sorted(PAPER_CARTESIAN_S):
+        for n in (64, 256):
+            db = synth.cartesian(seed=6, m=m, n=n)
+            dev = make_inputs(db, torch, "cuda")
+            rec = {"rows_per_relation": m, "cols_per_relation": n, "join_rows": m * m,
+                   "paper_figaro_mkl_s": PAPER_CARTESIAN_S[m][n]}
+            for tag, prec in (("fp64", binding.FIGARO_PREC_FP64), ("mixed", binding.FIGARO_PREC_MIXED)):
+                p = one_plan(binding, torch, dev, db.parent, stream, precision=prec)
+                rec[tag + "_ms"] = time_steps(p, torch, args.steps, args.warmup, lambda: None)
+                p.close()
+            rec["paper_over_fp64"] = rec["paper_figaro_mkl_s"] * 1e3 / rec["fp64_ms"]
+            rows.append(rec)
+            del dev
+    print(json.dumps({"metric": "time to R, Cartesian product S x T (paper Exp. 1 grid)", "unit": "ms",
+                      "higher_is_better": False, "steps": args.steps, "warmup": args.warmup,
+                      "data": "synthetic U[-3,3) (seeded)", "paper_hardware": "Xeon Silver 4214, 24 cores, MKL",
+                      "grid": rows}), flush=True)
+
+
 def wide_workload(name):
     """The wide-block workloads: the 5M-row many-to-many star (16 columns per relation,
     a 48-column generalized-tail block of ~5M rows) and the 10M-row snowflake (50 columns per
@@ -781,6 +817,8 @@ def main():
                     help="workload of --plan-only")
     ap.add_argument("--wide", action="store_true",
                     help="measure the wide-block workloads (star, snowflake) instead")
+    ap.add_argument("--cartesian", action="store_true",
+                    help="measure the Cartesian-product grid of the paper's first experiment instead")
     ap.add_argument("--batch-instances", type=int, default=0,
                     help="measure the batched-instances workload (first K of 256) instead")
     args = ap.parse_args()
@@ -792,6 +830,8 @@ def main():
         run_batch(args)
     elif args.wide:
         run_wide(args)
+    elif args.cartesian:
+        run_cartesian(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -273,6 +273,9 @@ static void launch_givens(const TsqrBlock& b, cudaStream_t st) {
 // squares over the warp, which the next column's scalars need.
 constexpr int kFoldThreads = 288;
 constexpr int kFoldWorkers = 256;
+constexpr int kStackStage = 4;                 // the final stack fold: N <= 1024 (staging 4 per thread)
+constexpr int kStackFoldMaxN = 1024;
+constexpr int kStackMaxBlocks = 256;           // more blocks: none placed, every one folded
 constexpr int kFoldPivotWarp = kFoldWorkers / 32;
 constexpr int kFoldMaxSlices = 8;
 constexpr size_t kFoldSmemF32 = 100 * 1024;   // two float blocks per SM (latency-bound)
@@ -353,7 +356,8 @@ __device__ __forceinline__ int fold_slices(int cols) {
 // staging row that the previous step filled when T is in global memory, tglob); the step
 // fills the staging row k+1 the same way, with its loads in flight through both passes.
 // rec (may be null) receives tau' and 1/v0 of the reflector.  Both passes end in a barrier.
-template <typename E>
+// ST: elements of a staged T row per thread (n <= ST x kFoldThreads when T is global).
+template <typename E, int ST = 1>
 __device__ __forceinline__ void fold_step(E* X, int ldx, int h, int P, int n, int k, int kend, int ra, int rb, E* T,
                                           bool tglob, E* red, E* rec) {
   const int tid = threadIdx.x, lane = tid & 31;
@@ -366,9 +370,12 @@ __device__ __forceinline__ void fold_step(E* X, int ldx, int h, int P, int n, in
   const E* xk = X + (int64_t)k * ldx;
   E* trk = T + (int64_t)k * n;
   const E* rowk = tglob ? tbuf + (k & 1) * n : trk;
-  E tn = E(0);
-  const bool pre = tglob && tid < n - k - 1;              // staging of T[k+1][k+1..n-1]
-  if (pre) tn = __ldcg(T + (int64_t)(k + 1) * n + k + 1 + tid);
+  E tn[ST];                                               // staging of T[k+1][k+1..n-1]
+#pragma unroll
+  for (int q = 0; q < ST; ++q) {
+    const int idx = tid + q * kFoldThreads;
+    tn[q] = (tglob && idx < n - k - 1) ? __ldcg(T + (int64_t)(k + 1) * n + k + 1 + idx) : E(0);
+  }
   if (tid < kFoldWorkers) {
     const int items = S * cp;
     for (int e = tid; e < items; e += kFoldWorkers) {
@@ -472,7 +479,11 @@ __device__ __forceinline__ void fold_step(E* X, int ldx, int h, int P, int n, in
       sc[2] = sq;
     }
   }
-  if (pre) tbuf[((k + 1) & 1) * n + k + 1 + tid] = tn;
+#pragma unroll
+  for (int q = 0; q < ST; ++q) {
+    const int idx = tid + q * kFoldThreads;
+    if (tglob && idx < n - k - 1) tbuf[((k + 1) & 1) * n + k + 1 + idx] = tn[q];
+  }
   __syncthreads();
 }
 
@@ -484,7 +495,8 @@ __device__ __forceinline__ void fold_column_start(const E* X, int ldx, int h, in
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   E* sc = red + (n > kFoldWorkers ? n : kFoldWorkers) + n;
   E* tbuf = sc + 4;
-  if (tglob && tid < n - k) tbuf[(k & 1) * n + k + tid] = __ldcg(T + (int64_t)k * n + k + tid);
+  if (tglob)
+    for (int idx = tid; idx < n - k; idx += kFoldThreads) tbuf[(k & 1) * n + k + idx] = __ldcg(T + (int64_t)k * n + k + idx);
   if (warp == kFoldPivotWarp) {
     const E* x0 = X + (int64_t)k * ldx;
     E sq = E(0);
@@ -503,7 +515,7 @@ __device__ __forceinline__ void fold_column_start(const E* X, int ldx, int h, in
 // leading dimension ldx).  Dense: every row may be non-zero.  tri: every row block holds
 // rows [r0, r0 + h) of an upper triangle, so that in column k only its first
 // k + 1 - r0 rows can be non-zero.
-template <typename E>
+template <typename E, int ST = 1>
 __device__ void fold_chunk(E* X, int ldx, int h, int P, int n, int r0, bool tri, E* T, bool tglob, E* red) {
   auto rows_at = [&](int k) -> int {
     if (!tri) return h;
@@ -516,7 +528,7 @@ __device__ void fold_chunk(E* X, int ldx, int h, int P, int n, int r0, bool tri,
   if (kbeg >= n) return;
   fold_column_start<E>(X, ldx, h, P, n, kbeg, rows_at(kbeg), T, tglob, red);
   for (int k = kbeg; k < n; ++k)
-    fold_step<E>(X, ldx, h, P, n, k, n, rows_at(k), rows_at(k + 1), T, tglob, red, nullptr);
+    fold_step<E, ST>(X, ldx, h, P, n, k, n, rows_at(k), rows_at(k + 1), T, tglob, red, nullptr);
 }
 
 // ------------------------------------------------------------------ tensor-core fold (float leaf)
@@ -896,12 +908,13 @@ __global__ void k_tsqr_stack(const TsqrBlock* blocks, int nb, int stack_rows, in
   }
 }
 
-// Final QR of the stacked block triangles by folding (n <= 256): the triangle of a block
-// that covers every column (the root's Data) becomes T as it is, and every other block
-// triangle, embedded at its global columns, is folded in as row pieces of an upper triangle:
-// row r of a block triangle is zero before global column cols[r] >= cols[0] + r, so a piece
-// starting at row p is the tri case of fold_chunk with r0 = cols[p].  The stack's zeros are
-// skipped, where the dense stack of S rows would cost 2 S N^2 flops in a leaf and a tree.
+// Final QR of the stacked block triangles by folding (N <= 1024, at most kStackMaxBlocks
+// blocks): the triangles of blocks with pairwise disjoint column sets are placed in T as
+// they are, and every other block triangle, embedded at its global columns, is folded in as
+// row pieces of an upper triangle: row r of a block triangle is zero before global column
+// cols[r] >= cols[0] + r, so a piece starting at row p is the tri case of fold_chunk with
+// r0 = cols[p].  The stack's zeros are skipped, where the dense stack of S rows would cost
+// 2 S N^2 flops in a leaf and a tree.
 __global__ void __launch_bounds__(kFoldThreads, 1)
     k_tsqr_stack_fold(const TsqrBlock* blocks, int nb, int N, int mc, int tsm, double* Tglob, double* tri_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -910,35 +923,69 @@ __global__ void __launch_bounds__(kFoldThreads, 1)
   const int ldx = mc + 1;
   double* T = tsm ? X + (int64_t)ldx * N : Tglob;
   const bool tglob = !tsm;
-  int full = -1;
-  for (int bi = 0; bi < nb && full < 0; ++bi) {
-    const TsqrBlock& b = blocks[bi];
-    if (b.n != N || block_rows(b) <= 0) continue;
-    bool ident = true;
-    for (int c = 0; c < N; ++c) ident = ident && b.cols[c] == c;
-    if (ident) full = bi;
+  // Blocks whose column sets are disjoint need no fold: their triangles are placed in T as
+  // they are (row r of a block lands in T's row cols[r], still upper triangular).  One
+  // thread picks them greedily by rank (non-zero rows of the triangle, min(n, live rows)),
+  // largest first; the others are folded in that order, each only over its non-zero rows.
+  __shared__ int order[kStackMaxBlocks];
+  __shared__ unsigned char placed[kStackMaxBlocks];
+  __shared__ uint32_t used[kStackFoldMaxN / 32];
+  __shared__ int n_order;
+  if (threadIdx.x == 0) {
+    int cnt = 0;
+    for (int bi = 0; bi < nb && bi < kStackMaxBlocks; ++bi) {
+      placed[bi] = 0;
+      if (block_rows(blocks[bi]) > 0) order[cnt++] = bi;
+    }
+    auto rank = [&](int bi) {
+      const int64_t r = block_rows(blocks[bi]);
+      return r < blocks[bi].n ? (int)r : blocks[bi].n;
+    };
+    for (int i = 0; i < cnt; ++i)                    // selection sort, rank descending
+      for (int j = i + 1; j < cnt; ++j)
+        if (rank(order[j]) > rank(order[i])) { const int t = order[i]; order[i] = order[j]; order[j] = t; }
+    for (int w = 0; w < (N + 31) / 32; ++w) used[w] = 0u;
+    for (int i = 0; i < cnt; ++i) {
+      const TsqrBlock& b = blocks[order[i]];
+      bool free_cols = nb <= kStackMaxBlocks;
+      for (int c = 0; c < b.n && free_cols; ++c) free_cols = !(used[b.cols[c] >> 5] & (1u << (b.cols[c] & 31)));
+      if (!free_cols) continue;
+      placed[order[i]] = 1;
+      for (int c = 0; c < b.n; ++c) used[b.cols[c] >> 5] |= 1u << (b.cols[c] & 31);
+    }
+    n_order = cnt;
   }
-  const double* tf = full >= 0 ? blocks[full].tri[blocks[full].top] : nullptr;
-  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
-    const int r = idx / N, c = idx - r * N;          // T is row-major
-    T[idx] = (tf && r <= c) ? tf[(int64_t)c * N + r] : 0.0;
-  }
+  for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) T[idx] = 0.0;
   __syncthreads();
-  for (int bi = 0; bi < nb; ++bi) {
-    const TsqrBlock& b = blocks[bi];
-    if (bi == full || block_rows(b) <= 0) continue;
+  for (int i = 0; i < n_order; ++i) {
+    const TsqrBlock& b = blocks[order[i]];
+    if (!placed[order[i]]) continue;
     const int n = b.n;
     const double* tri = b.tri[b.top];               // column-major n x n, upper
-    for (int p = 0; p < n; p += mc) {
-      const int h = (n - p) < mc ? (n - p) : mc;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      const int c = idx / n, r = idx - c * n;
+      if (r <= c) T[(int64_t)b.cols[r] * N + b.cols[c]] = tri[idx];
+    }
+  }
+  __syncthreads();
+  for (int i = 0; i < n_order; ++i) {
+    const int bi = order[i];
+    if (placed[bi]) continue;
+    const TsqrBlock& b = blocks[bi];
+    const int n = b.n;
+    const int64_t live = block_rows(b);
+    const int nz = live < n ? (int)live : n;        // the triangle's rows below nz are zero
+    const double* tri = b.tri[b.top];               // column-major n x n, upper
+    for (int p = 0; p < nz; p += mc) {
+      const int h = (nz - p) < mc ? (nz - p) : mc;
       for (int idx = threadIdx.x; idx < ldx * N; idx += blockDim.x) X[idx] = 0.0;
       __syncthreads();
       for (int idx = threadIdx.x; idx < h * n; idx += blockDim.x) {
-        const int c = idx / h, i = idx - c * h;     // local column c, piece row i (block row p + i)
-        if (p + i <= c) X[(int64_t)b.cols[c] * ldx + i] = tri[(int64_t)c * n + p + i];
+        const int c = idx / h, r = idx - c * h;     // local column c, piece row r (block row p + r)
+        if (p + r <= c) X[(int64_t)b.cols[c] * ldx + r] = tri[(int64_t)c * n + p + r];
       }
       __syncthreads();
-      fold_chunk<double>(X, ldx, h, 1, N, b.cols[p], true, T, tglob, red);
+      fold_chunk<double, kStackStage>(X, ldx, h, 1, N, b.cols[p], true, T, tglob, red);
     }
   }
   for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
@@ -954,7 +1001,7 @@ static void stack_fold_plan(int N, int& mc, int& tsm, size_t& smem) {
   tsm = tbytes <= kSmemCap / 4 ? 1 : 0;
   const size_t rest = kSmemCap - red - (tsm ? tbytes : 0);
   int64_t m = (int64_t)(rest / (sizeof(double) * (size_t)N)) - 1;
-  m = (m / 32) * 32;
+  m = m >= 32 ? (m / 32) * 32 : (m / 8) * 8;  // rows per piece: at least 16 up to N = 1024
   if (m > 512) m = 512;
   mc = (int)m;
   smem = red + (size_t)(mc + 1) * N * sizeof(double) + (tsm ? tbytes : 0);
@@ -1219,7 +1266,7 @@ void tsqr_final(const TsqrBlock* blocks_dev, int n_blocks, TsqrBlock& stack_blk,
   const int N = stack_blk.n;
   // Up to 32 columns the dense stack goes through the register leaf in a launch or two,
   // which beats the fold's single block walking the pieces one Householder step at a time.
-  if (N > 32 && N <= kFoldWorkers) {
+  if (N > 32 && N <= kStackFoldMaxN && n_blocks <= kStackMaxBlocks) {
     int mc = 0, tsm = 0;
     size_t smem = 0;
     stack_fold_plan(N, mc, tsm, smem);
