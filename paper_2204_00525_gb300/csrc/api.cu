@@ -1144,6 +1144,7 @@ int figaro_plan(const figaro_join_tree* tree, const figaro_options* opt, void* s
     cudaError_t e = keys_set_attributes();
     if (e == cudaSuccess) e = tsqr_set_attributes();
     if (e == cudaSuccess) e = svd_set_attributes();
+    if (e == cudaSuccess) e = rows_of_set_attributes();
     if (e == cudaSuccess) e = refine_set_attributes();
     if (e != cudaSuccess) {
       delete P;

@@ -126,9 +126,49 @@ __global__ void __launch_bounds__(256) k_rows_of(const double* src, int64_t ld, 
   }
 }
 
+// Tables of at most kSlabCols columns: a warp copies a slab of 32 rows and all columns,
+// lanes over rows for the loads (one coalesced 256-byte segment per column, all of them in
+// flight) and over columns for the stores (whole rows), through its own shared-memory slab.
+constexpr int kSlabCols = 64;
+
+__global__ void __launch_bounds__(256) k_rows_of_slab(const double* src, int64_t ld, int64_t bound,
+                                                      const int32_t* live, int cols, double* dst, int np) {
+  extern __shared__ double slab_all[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ls = cols + 1;                           // odd stride: the row-wise stores hit distinct banks
+  double* slab = slab_all + (int64_t)warp * 32 * ls;
+  const int64_t rows = live ? (int64_t)live[0] : bound;
+  const int64_t slabs = (rows + 31) >> 5;
+  for (int64_t q = (int64_t)blockIdx.x * 8 + warp; q < slabs; q += (int64_t)gridDim.x * 8) {
+    const int64_t r0 = q * 32, r = r0 + lane;
+#pragma unroll 16
+    for (int c = 0; c < cols; ++c) slab[lane * ls + c] = r < rows ? src[(int64_t)c * ld + r] : 0.0;
+    __syncwarp();
+    const int nr = (rows - r0) < 32 ? (int)(rows - r0) : 32;
+    for (int i = 0; i < nr; ++i)
+      for (int c = lane; c < cols; c += 32) dst[(r0 + i) * np + c] = slab[i * ls + c];
+    __syncwarp();
+  }
+}
+
+size_t rows_of_slab_smem() { return (size_t)8 * 32 * (kSlabCols + 1) * sizeof(double); }
+
+cudaError_t rows_of_set_attributes() {
+  return cudaFuncSetAttribute(k_rows_of_slab, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_of_slab_smem());
+}
+
 void rows_of(const double* src, int64_t ld, int64_t bound, const int32_t* live, int cols, double* dst, int np,
              cudaStream_t st, int64_t* launches) {
   if (cols <= 0 || bound <= 0) return;
+  if (cols <= kSlabCols) {
+    const int64_t slabs = (bound + 31) / 32;
+    int64_t blocks = (slabs + 7) / 8;
+    if (blocks > 152 * 2) blocks = 152 * 2;
+    const size_t smem = (size_t)8 * 32 * (cols + 1) * sizeof(double);
+    k_rows_of_slab<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, smem, st>>>(src, ld, bound, live, cols, dst, np);
+    ++*launches;
+    return;
+  }
   const int64_t tiles = ((bound + 31) / 32) * ((cols + 31) / 32);
   k_rows_of<<<(unsigned)(tiles < 152 * 8 ? tiles : 152 * 8), 256, 0, st>>>(src, ld, bound, live, cols, dst, np);
   ++*launches;

@@ -201,6 +201,7 @@ struct GenParams {
 void beta_table(double2* beta, int64_t len, cudaStream_t st);
 // Row moves for the gathers: a row-major copy of a column-major table (rows beyond *live,
 // if given, are skipped), and the sorted copy out[c][e] = rows[perm[e]][c].
+cudaError_t rows_of_set_attributes();   // the slab copy's shared memory (up to 133 KB)
 void rows_of(const double* src, int64_t ld, int64_t bound, const int32_t* live, int cols, double* dst, int np,
              cudaStream_t st, int64_t* launches);
 void rows_gather(const double* rows, int64_t rs, const int32_t* perm, int64_t M, int cols, double* out,
