@@ -5,10 +5,12 @@
 // hold a sixth of a relation, so here the sorted rows are cut into fixed tiles of
 // 256 elements per warp regardless of group boundaries.  Per column, a prefix sum that
 // restarts at every group start is computed in three steps: (1) every tile reports
-// whether it contains a group start and the sum after its last start, and every lane its
-// exclusive (flag, sum) inside the tile, (2) one thread block per column scans the tile
-// aggregates into a carry per tile, (3) every lane starts its running sum at its carry and
-// writes tail rows and heads (one add, one FMA and one multiply per cell).
+// whether it contains a group start and the sum after its last start, every lane its
+// exclusive (flag, sum) inside the tile, and the heads of the groups that begin in the
+// tile are written final, (2) one thread block per column scans the tile aggregates into a
+// carry per tile, which also completes the one group per tile that began earlier, (3)
+// every lane starts its running sum at its carry and writes the tail rows (one add, one FMA
+// and one multiply per cell), skipping tiles without a tail row.
 //
 // Tail of a group with rows a_0..a_{m-1} (0-based position p, exclusive prefix S_p):
 //   row p >= 1:  sqrt(Phi_circ) (sqrt(p) a_p - S_p / sqrt(p)) / sqrt(p + 1)
