@@ -108,3 +108,26 @@ def test_struct_layouts_match_header():
     assert C.sizeof(binding.figaro_join_tree) == 24
     assert C.sizeof(binding.figaro_options) == 64
     assert C.sizeof(binding.figaro_plan_info) == 64
+
+
+def test_option_values_are_checked_before_any_device_work(lib):
+    """fuse_tails and autotune accept 0 or 1 only; the check comes before any CUDA call."""
+    from paper_2204_00525_gb300 import binding
+    for field, bad in (("fuse_tails", 2), ("autotune", -1), ("leaf", 7), ("precision", 5)):
+        tree, keep = _tree(binding, [_rel([0]), _rel([0])], [-1, 0])
+        opt = binding.figaro_default_options()
+        opt.mem = binding.FIGARO_MEM_HOST
+        setattr(opt, field, bad)
+        h = C.c_void_p()
+        assert lib.figaro_plan(C.byref(tree), C.byref(opt), None, C.byref(h)) == 1, field
+        assert not h.value
+
+
+def test_options_struct_matches_header_field_order():
+    """The ctypes mirror of figaro_options lists the header's fields in the header's order."""
+    import re
+    from paper_2204_00525_gb300 import binding
+    hdr = open(os.path.join(ROOT, "include", "figaro.h")).read()
+    body = re.search(r"typedef struct figaro_options \{(.*?)\} figaro_options;", hdr, re.S).group(1)
+    names = re.findall(r"int32_t\s+(\w+)(?:\[\d+\])?;", body)
+    assert names == [f[0] for f in binding.figaro_options._fields_]
