@@ -751,8 +751,9 @@ struct FoldLeafTc<float> {
   }
 };
 
-// level 0: the leaf over the block's rows; level l > 0: tree level l over tri_in.
-template <typename E>
+// level 0: the leaf over the block's rows; level l > 0: tree level l over tri_in.  ST: T-row
+// staging per thread (4 for blocks wider than the 256 worker threads, up to 1,024 columns).
+template <typename E, int ST = 1>
 __global__ void __launch_bounds__(kFoldThreads, sizeof(E) == 4 ? 2 : 1)
     k_tsqr_fold(TsqrBlock b, const double* tri_in, double* tri_out, int level) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -821,7 +822,7 @@ __global__ void __launch_bounds__(kFoldThreads, sizeof(E) == 4 ? 2 : 1)
         }
         __syncthreads();
         if (!(tc && FoldLeafTc<E>::run(X, ldx, m, n, T, tglob, red, ext)))
-          fold_chunk<E>(X, ldx, m, 1, n, 0, false, T, tglob, red);
+          fold_chunk<E, ST>(X, ldx, m, 1, n, 0, false, T, tglob, red);
       }
     } else if (stack >= 2) {
       for (int64_t q = qs; q < q1; q += stack) {
@@ -834,7 +835,7 @@ __global__ void __launch_bounds__(kFoldThreads, sizeof(E) == 4 ? 2 : 1)
           }
         }
         __syncthreads();
-        fold_chunk<E>(X, ldx, n, cnt, n, 0, true, T, tglob, red);
+        fold_chunk<E, ST>(X, ldx, n, cnt, n, 0, true, T, tglob, red);
       }
     } else {
       for (int64_t q = qs; q < q1; ++q) {
@@ -846,7 +847,7 @@ __global__ void __launch_bounds__(kFoldThreads, sizeof(E) == 4 ? 2 : 1)
             for (int i = lane; i < m; i += 32) dst[i] = (E)src[(int64_t)c * n + r0 + i];
           }
           __syncthreads();
-          fold_chunk<E>(X, ldx, m, 1, n, r0, true, T, tglob, red);
+          fold_chunk<E, ST>(X, ldx, m, 1, n, r0, true, T, tglob, red);
         }
       }
     }
@@ -884,7 +885,11 @@ static void launch_fold(const TsqrBlock& b, const double* tri_in, double* tri_ou
   int64_t grid = fold_units(b, level);
   const int64_t cap = b.fold_res > 0 ? b.fold_res : fold_resident(mixed);
   if (grid > cap) grid = cap;
-  k_tsqr_fold<E><<<(unsigned)grid, kFoldThreads, fold_smem(b, sizeof(E)), st>>>(b, tri_in, tri_out, level);
+  if (b.n > kFoldWorkers)
+    k_tsqr_fold<E, kStackStage><<<(unsigned)grid, kFoldThreads, fold_smem(b, sizeof(E)), st>>>(b, tri_in, tri_out,
+                                                                                               level);
+  else
+    k_tsqr_fold<E><<<(unsigned)grid, kFoldThreads, fold_smem(b, sizeof(E)), st>>>(b, tri_in, tri_out, level);
 }
 
 // ------------------------------------------------------------------ final stack and R
@@ -1044,19 +1049,20 @@ static size_t cta_smem(int lda, int n, size_t esz) { return (kRedElems + (size_t
 // the float path, whose error grows with the number of folds into one triangle).
 static bool fold_plan(TsqrBlock& b, bool mixed, size_t esz, bool tcgen05, const TsqrTune* tn) {
   const int n = b.n;
-  if (n > kFoldWorkers) return false;          // T rows are staged one element per worker thread
+  if (n > kStackFoldMaxN) return false;        // T rows are staged at most four elements per thread
+  const bool wide = n > kFoldWorkers;          // no tensor-core panels (their staging is per worker)
   size_t budget = fold_budget(mixed);
   if (tn && tn->fold_budget_kib > 0 && (size_t)tn->fold_budget_kib * 1024 < budget)
     budget = (size_t)tn->fold_budget_kib * 1024;
-  const bool tc = mixed;                      // float leaf: tensor-core panels
+  const bool tc = mixed && !wide;             // float leaf: tensor-core panels
   const size_t red = ((size_t)fold_red_elems(n) + (tc ? (size_t)fold_tc_extra(n) : 0)) * esz;
   if (red >= budget) return false;
   const bool tsm = (size_t)n * n * esz <= budget / 4;
   const size_t rest = budget - red - (tsm ? (size_t)n * n * esz : 0);
   int64_t mc = (int64_t)(rest / (esz * (size_t)n)) - (tc ? 4 : 1);
-  mc = (mc / 32) * 32;
+  mc = (wide && mc < 32) ? (mc / 16) * 16 : (mc / 32) * 32;   // wide blocks: chunks of 16 rows at least
   if (mc > 512) mc = 512;
-  if (mc < 32) return false;
+  if (mc < (wide ? 16 : 32)) return false;
   b.fold = true;
   b.fold_tsmem = tsm;
   b.fold_tc = tc;
@@ -1065,7 +1071,7 @@ static bool fold_plan(TsqrBlock& b, bool mixed, size_t esz, bool tcgen05, const 
   // the float leaf on tcgen05 where its shared-memory layout fits (unless the mma.sync
   // fold was asked for): 128-row chunks (the tree levels fold with the same chunk height),
   // one thread block per SM
-  b.fold_tc5 = tcgen05 && mixed && fold_tc_fits(n);
+  b.fold_tc5 = tcgen05 && mixed && !wide && fold_tc_fits(n);
   if (b.fold_tc5) {
     b.fold_tc = false;
     b.tile = 128;
@@ -1189,6 +1195,12 @@ cudaError_t tsqr_set_attributes() {
     e = cudaFuncSetAttribute(k_tsqr_fold<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_tsqr_fold<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tsqr_fold<double, kStackStage>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSmemCap);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tsqr_fold<float, kStackStage>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSmemCap);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_tsqr_stack_fold, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
   if (e == cudaSuccess) e = fold_tc_set_attributes();
