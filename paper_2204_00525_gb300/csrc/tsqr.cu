@@ -14,9 +14,11 @@
 //   n <= 32:       one warp per tile, the tile in registers (k_tsqr_reg), every loop bound
 //                  a compile-time constant so that no predicated-off FP64 instruction is
 //                  issued; levels with few tiles take one thread block per tile (k_tsqr_cta);
-//   33 <= n <= 256: the streamed fold (k_tsqr_fold): one resident triangle per thread block,
-//                  row chunks folded into it, structured tree levels;
-//   n > 256:       one thread block per tile in shared memory or a global slot (k_tsqr_cta).
+//   33 <= n <= 1024: the streamed fold (k_tsqr_fold): one resident triangle per thread
+//                  block, row chunks folded into it, structured tree levels (above 256
+//                  columns the triangle sits in a global slot, its rows staged four
+//                  elements per thread, and chunks are 16 to 64 rows high);
+//   otherwise:     one thread block per tile in shared memory or a global slot (k_tsqr_cta).
 // All are persistent over the live tiles: the row counts are only known on the device.
 //
 // Precision: FP64 throughout, or (mixed) FP32 leaf tiles and tree levels with the final QR
@@ -1060,7 +1062,7 @@ static bool fold_plan(TsqrBlock& b, bool mixed, size_t esz, bool tcgen05, const 
   const bool tsm = (size_t)n * n * esz <= budget / 4;
   const size_t rest = budget - red - (tsm ? (size_t)n * n * esz : 0);
   int64_t mc = (int64_t)(rest / (esz * (size_t)n)) - (tc ? 4 : 1);
-  mc = (wide && mc < 32) ? (mc / 16) * 16 : (mc / 32) * 32;   // wide blocks: chunks of 16 rows at least
+  mc = (wide && mc < 32) ? (mc / 16) * 16 : (mc / 32) * 32;   // wide blocks: 16-row chunks at least
   if (mc > 512) mc = 512;
   if (mc < (wide ? 16 : 32)) return false;
   b.fold = true;

@@ -1,13 +1,13 @@
-"""Blocks of 33-256 columns, reduced by the streamed fold (k_tsqr_fold), and the first
-width past it (k_tsqr_cta), against the oracle.  Two-relation joins S(a) - T(a) whose
+"""Blocks of 33-1024 columns, reduced by the streamed fold (k_tsqr_fold), against the
+oracle.  Two-relation joins S(a) - T(a) whose
 root block has n_S + n_T columns and whose tails blocks have n_S and n_T columns:
 
   multichunk   199k-row tails of 40 columns: every leaf triangle folds several chunks,
                two tree levels of stacked triangles; R^T R against the factorized Gram
   short_root   a 200-column root block of 100 rows (fewer rows than columns: the rounding
                residue reaches subnormal sums of squares), 100-column tails
-  width_256    the widest fold block (256 columns)
-  width_257    one column more: the block-per-tile path
+  width_256    the widest block whose T rows take one element per worker thread
+  width_257    one column more: T rows staged four elements per thread, 64-row chunks
   zero_column  a data column of zeros (sigma = 0: the reflector is skipped; R^T R only,
                as R is not unique)
   dup_column   two equal columns (rank deficient: R^T R only)
