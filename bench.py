@@ -55,7 +55,7 @@ GOLDEN_GRAM = os.path.join(ROOT, "tests", "golden", "snowflake_gram.npz")
 # generalized-tail block): (dram__bytes_read.sum + dram__bytes_write.sum) / rows of the ncu
 # capture of the same kernel on the snowflake with a fifth of the rows, summarised in
 # profiles/tsqr_fold_f64_snowflake.md; the traffic grows with the rows.
-DOMINANT_DRAM_BYTES_PER_ROW = (1.442287e9 + 8.885248e6) / 1_799_944
+DOMINANT_DRAM_BYTES_PER_ROW = (1.443330e9 + 9.190912e6) / 1_799_944
 
 
 def log(*a):
