@@ -145,8 +145,9 @@ typedef struct figaro_join_tree {
  *                    SM, chunks per leaf triangle and tree fan follow the planner's rules
  *                    (width, precision, shared-memory budget).  1: figaro_plan times a few
  *                    candidate plans per block (the rule's among them) on synthetic rows
- *                    of the block's width and row bound (at most 2^30 cells) and keeps the
- *                    fastest; results are cached per (precision, leaf, width, row bucket)
+ *                    of the block's width and row bound (at most 2^30 cells and
+ *                    rows x width^2 <= 2^37) and keeps the fastest; results are cached
+ *                    per (precision, leaf, width, row bucket)
  *                    for the process, so equal shapes are tuned once.  The same R up to
  *                    rounding (the float path keeps its bound of 16 chunks per leaf
  *                    triangle).  Any other value: INVALID_ARG.                        */

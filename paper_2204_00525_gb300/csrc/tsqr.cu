@@ -1109,6 +1109,11 @@ static bool fold_plan(TsqrBlock& b, bool mixed, size_t esz, bool tcgen05, const 
 void tsqr_plan_block(TsqrBlock& b, bool mixed, bool givens, bool tcgen05, const TsqrTune* tune) {
   const int n = b.n;
   const size_t esz = mixed ? sizeof(float) : sizeof(double);
+  // a block may be planned again (the autotuner's choice after the rule): the fold fields of
+  // an earlier plan must not survive into a plan of another path
+  b.fold = b.fold_tsmem = b.fold_tc = b.fold_tc5 = false;
+  b.seg = b.fold_g0 = 0;
+  b.fold_res = 0;
   b.nreg = reg_class(n);
   b.givens = givens && b.nreg && b.nreg <= 16;
   b.fused = b.fused && b.kind == BLK_TAILS && b.nreg && !b.givens;

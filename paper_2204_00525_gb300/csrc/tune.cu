@@ -2,10 +2,12 @@
 // chunk height, blocks per SM, chunks per leaf triangle and tree fan from its width,
 // precision and the shared-memory budget; with autotune, figaro_plan instead times a small
 // set of candidate plans for each block on synthetic rows of the block's width and row
-// bound (at most 2^30 cells, uniform values from a counter-based generator) and keeps the
-// fastest, the rule's own plan among them.  Only the speed depends on the choice: every
-// candidate is an exact Householder TSQR of the same rows (on the float path the chunks
-// per leaf triangle stay at most 16, the bound that keeps its error within the stated one).
+// bound (at most 2^30 cells and rows x width^2 <= 2^37, so that one timed run stays within
+// about a third of a second in FP64 at any width; uniform values from a counter-based
+// generator) and keeps the fastest, the rule's own plan among them.  Only the speed
+// depends on the choice: every candidate is an exact Householder TSQR of the same rows (on
+// the float path the chunks per leaf triangle stay at most 16, the bound that keeps its
+// error within the stated one).
 // Results are cached per (precision, leaf kind, width, power-of-two row bucket) for the
 // life of the process, so plans of equal shapes (a batch's instances) are tuned once.
 #include <algorithm>
@@ -32,6 +34,7 @@ __global__ void k_tune_fill(double* d, float* f, int64_t n, uint64_t seed) {
 }
 
 constexpr int64_t kTuneCellsCap = int64_t(1) << 30;   // 8 GiB of float64 rows at most
+constexpr int64_t kTuneMacCap = int64_t(1) << 37;     // rows x n^2 of one timed run
 constexpr int64_t kFarAway = int64_t(1) << 40;   // warp_min that leaves every level to the block kernel
 
 // Candidate overrides for block b (the all-zero override, the rule's plan, first).
@@ -75,7 +78,9 @@ static std::map<TuneKey, TsqrTune> g_tune_cache;
 TsqrTune tsqr_autotune(const TsqrBlock& b, bool mixed, bool givens, bool tcgen05) {
   const TsqrTune none{0, 0, 0, 0};
   if (b.n < 1 || b.fused) return none;
-  const int64_t cap = kTuneCellsCap / b.n;
+  if (cudaPeekAtLastError() != cudaSuccess) return none;   // an earlier error stays for the caller
+  int64_t cap = kTuneCellsCap / b.n;
+  if (cap > kTuneMacCap / ((int64_t)b.n * b.n)) cap = kTuneMacCap / ((int64_t)b.n * b.n);
   const int64_t rows = b.bound < cap ? (b.bound > 0 ? b.bound : 1) : cap;
   int bucket = 0;
   while ((int64_t(1) << bucket) < rows) ++bucket;
@@ -144,7 +149,10 @@ TsqrTune tsqr_autotune(const TsqrBlock& b, bool mixed, bool givens, bool tcgen05
              cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
         if (rep > 0) total += ms;
       }
-      if (ok && (best_ms < 0.0 || total < best_ms)) {
+      // a launch the device refused (its configuration) disqualifies the candidate only;
+      // an error that persists fails the event calls above and ends the tuning
+      const bool ran = cudaGetLastError() == cudaSuccess;
+      if (ok && ran && (best_ms < 0.0 || total < best_ms)) {
         best_ms = total;
         best = cand[i];
       }

@@ -1,8 +1,9 @@
 """options.autotune: the TSQR plan of every block picked by timing candidate plans on
 synthetic rows at plan time.  The tuned plans must give the oracle's R (FP64: relative
 Frobenius error 1e-10; mixed: R^T R within 1e-6 of A^T A) on blocks of every TSQR path:
-the register leaf (<= 16 and 17-32 columns), the FP64 fold, the float fold and the tcgen05
-leaf; equal shapes are tuned once per process (the second plan is built from the cache)."""
+the register leaf (<= 16 and 17-32 columns), the FP64 fold, the float fold, the tcgen05
+leaf and the fold of blocks wider than 256 columns; equal shapes are tuned once per process
+(the second plan is built from the cache)."""
 import time
 
 import numpy as np
@@ -39,6 +40,9 @@ CASES = {
     "reg_wide": lambda: synth.two_relation(seed=82, rows=30000, keys=200, n_s=24, n_t=28),
     "fold": lambda: synth.two_relation(seed=83, rows=60000, keys=500, n_s=40, n_t=70),
     "fold_wide": lambda: synth.two_relation(seed=84, rows=20000, keys=100, n_s=150, n_t=20),
+    # blocks of 300, 400 and 700 columns: T rows staged four per thread; the FP64 candidate
+    # with a 64 KiB budget leaves no room for a fold chunk and runs a thread block per tile
+    "fold_over_256": lambda: synth.two_relation(seed=86, rows=3000, keys=60, n_s=300, n_t=400),
     "snowflake_small": lambda: synth.snowflake(f_rows=100000, d1_rows=20000, d2_rows=15000, d3_rows=3000,
                                                n_cols=12, n_scaled=2),
 }
