@@ -129,7 +129,7 @@ TsqrTune tsqr_autotune(const TsqrBlock& b, bool mixed, bool givens, bool tcgen05
   TsqrTune best = none;
   if (ok) {
     k_tune_fill<<<grid_for(cells, 256, 152 * 8), 256, 0, st>>>(data, data32, cells, 0x5eedull + (uint64_t)b.n);
-    ok = cudaMemsetAsync(err, 0, sizeof(int), st) == cudaSuccess;
+    ok = cudaGetLastError() == cudaSuccess && cudaMemsetAsync(err, 0, sizeof(int), st) == cudaSuccess;
     double best_ms = -1.0;
     for (size_t i = 0; ok && i < plans.size(); ++i) {
       TsqrBlock p = plans[i];
